@@ -1,0 +1,399 @@
+"""Pins of the FP64 CPU oracle against facts fixed by physics and mathematics.
+
+None of these re-types the oracle's formulas: each compares it with a closed
+form, a symmetry, a conservation law, a finite-difference derivative or an
+extended-precision brute force, chosen so that a dropped term, a wrong sign or
+exponent, or a transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_5234_gb300 import inputs
+
+
+# ---------------------------------------------------------------- force ---
+
+def test_two_body_exact_values():
+    # d = 3, eps = 4: (d^2 + eps^2)^(1/2) = 5 exactly, so |a| = G m d / 125 and
+    # phi = -G m / 5 exactly (Eq. 2 and the potential it derives from).
+    pos = np.array([[0.0, 0, 0], [3.0, 0, 0]])
+    vel = np.zeros((2, 3))
+    mass = np.array([2.0, 5.0])
+    acc, jerk, pot = oracle.force(pos, vel, mass, eps=4.0, G=1.0)
+    assert acc[0] == pytest.approx([5.0 * 3 / 125, 0, 0], abs=1e-16)
+    assert acc[1] == pytest.approx([-2.0 * 3 / 125, 0, 0], abs=1e-16)
+    assert pot == pytest.approx([-5.0 / 5, -2.0 / 5], rel=1e-15)
+    assert np.all(jerk == 0.0)
+    # unsoftened unit case: attraction toward the other body, |a| = 1
+    acc, _, pot = oracle.force(np.array([[0, 0, 0], [0, 0, 1.0]]), vel,
+                               np.array([1.0, 1.0]), eps=0.0)
+    assert acc[0].tolist() == [0.0, 0.0, 1.0]
+    assert acc[1].tolist() == [0.0, 0.0, -1.0]
+    assert pot.tolist() == [-1.0, -1.0]
+
+
+def test_G_scales_linearly():
+    cl = inputs.plummer(64, seed=3)
+    a1, j1, p1 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2, G=1.0)
+    a2, j2, p2 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2, G=2.5)
+    # compensated sums: equal up to a few ulps of each vector's norm
+    for x2, x1 in ((a2, a1), (j2, j1)):
+        nrm = np.linalg.norm(x1, axis=1, keepdims=True)
+        assert np.all(np.abs(x2 - 2.5 * x1) <= 4e-16 * 2.5 * nrm)
+    np.testing.assert_allclose(p2, 2.5 * p1, rtol=1e-15)
+
+
+def test_lagrange_equilateral_triangle():
+    # Three equal masses on an equilateral triangle of side L: each is pulled
+    # toward the centroid with |a| = sqrt(3) G m / L^2 (vector geometry).
+    L, m = 0.7, 1.3
+    pos = np.array([[0, 0, 0], [L, 0, 0], [L / 2, L * math.sqrt(3) / 2, 0]])
+    acc, _, _ = oracle.force(pos, np.zeros((3, 3)), np.full(3, m), eps=0.0)
+    c = pos.mean(0)
+    for i in range(3):
+        u = (c - pos[i]) / np.linalg.norm(c - pos[i])
+        np.testing.assert_allclose(acc[i], math.sqrt(3) * m / L ** 2 * u,
+                                   rtol=1e-14, atol=1e-15)
+
+
+def _icosahedron(radius):
+    p = (1 + math.sqrt(5)) / 2
+    v = []
+    for a in (-1, 1):
+        for b in (-p, p):
+            v += [(0, a, b), (a, b, 0), (b, 0, a)]
+    v = np.array(v, dtype=np.float64)
+    return radius * v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def test_shell_theorem_icosahedron():
+    # The 12 vertices of an icosahedron form a spherical 5-design: the shell's
+    # exterior field equals that of a point mass up to degree-6 multipoles,
+    # so at distance R = 20 r it matches G M / R^2 to ~ (r/R)^6 ~ 1e-8, and the
+    # potential matches -G M / R.  At the centre the pull cancels exactly by
+    # symmetry.
+    r, R = 0.05, 1.0
+    shell = _icosahedron(r)
+    mshell = np.full(12, 1.0 / 12)
+    probe = np.array([[0.3 * R, -0.4 * R, math.sqrt(0.75) * R]])
+    pos = np.vstack([shell, probe, [[0.0, 0.0, 0.0]]])
+    mass = np.concatenate([mshell, [0.0, 0.0]])
+    vel = np.zeros((14, 3))
+    acc, _, pot = oracle.force(pos, vel, mass, eps=0.0, idx=[12, 13])
+    np.testing.assert_allclose(acc[0], -probe[0] / R ** 3, rtol=1e-7)
+    assert pot[0] == pytest.approx(-1.0 / R, rel=1e-7)
+    np.testing.assert_allclose(acc[1], 0.0, atol=1e-13)
+    assert pot[1] == pytest.approx(-1.0 / r, rel=1e-14)
+
+
+def test_newton_third_law():
+    cl = inputs.plummer(300, seed=7, imf="kroupa")
+    acc, jerk, _ = oracle.force(cl.pos, cl.vel, cl.mass, eps=1e-3)
+    m = cl.mass[:, None]
+    scale_a = np.abs(m * acc).sum()
+    scale_j = np.abs(m * jerk).sum()
+    assert np.abs((m * acc).sum(0)).max() < 1e-14 * scale_a
+    assert np.abs((m * jerk).sum(0)).max() < 1e-14 * scale_j
+
+
+def test_acceleration_is_minus_gradient_of_potential():
+    # a_i = -grad_i phi_i, checked by a 4th-order central difference of the
+    # oracle's own potential (pins acc against pot: a wrong exponent or sign
+    # in either one fails).
+    cl = inputs.plummer(40, seed=11)
+    eps = 0.05
+    idx = [0, 5, 17, 39]
+    acc, _, _ = oracle.force(cl.pos, cl.vel, cl.mass, eps, idx=idx)
+    h = 1e-3
+    for k, i in enumerate(idx):
+        g = np.zeros(3)
+        for c in range(3):
+            vals = []
+            for s in (-2, -1, 1, 2):
+                p = cl.pos.copy()
+                p[i, c] += s * h
+                vals.append(oracle.force(p, cl.vel, cl.mass, eps, idx=[i])[2][0])
+            g[c] = (vals[0] - 8 * vals[1] + 8 * vals[2] - vals[3]) / (12 * h)
+        np.testing.assert_allclose(acc[k], -g, rtol=1e-8, atol=1e-9 * np.abs(acc[k]).max())
+
+
+def test_jerk_is_time_derivative_of_acceleration():
+    # Along straight-line motion x_j(t) = x_j + v_j t the exact d/dt of the
+    # softened acceleration at t = 0 is the jerk (it depends on x and v only).
+    cl = inputs.plummer(40, seed=12)
+    eps = 0.05
+    idx = [1, 9, 33]
+    _, jerk, _ = oracle.force(cl.pos, cl.vel, cl.mass, eps, idx=idx)
+    h = 1e-3
+    vals = [oracle.force(cl.pos + s * h * cl.vel, cl.vel, cl.mass, eps, idx=idx)[0]
+            for s in (-2, -1, 1, 2)]
+    fd = (vals[0] - 8 * vals[1] + 8 * vals[2] - vals[3]) / (12 * h)
+    np.testing.assert_allclose(jerk, fd, rtol=1e-7, atol=1e-8 * np.abs(jerk).max())
+
+
+def test_circular_orbit_jerk_closed_form():
+    # Two-body circular orbit: each body moves uniformly on a circle about the
+    # centre of mass, so a = -w^2 x and da/dt = -w^2 v, w^2 = G M / r^3.
+    m1, m2, r = 0.7, 0.3, 1.7
+    M = m1 + m2
+    w = math.sqrt(M / r ** 3)
+    pos = np.array([[-m2 / M * r, 0, 0], [m1 / M * r, 0, 0]])
+    vel = np.array([[0, -m2 / M * r * w, 0], [0, m1 / M * r * w, 0]])
+    acc, jerk, _ = oracle.force(pos, vel, np.array([m1, m2]), eps=0.0)
+    np.testing.assert_allclose(acc, -w * w * pos, rtol=1e-14, atol=1e-16)
+    np.testing.assert_allclose(jerk, -w * w * vel, rtol=1e-14, atol=1e-16)
+
+
+def test_brute_force_extended_precision():
+    # 50-digit brute force on a tiny system bounds the oracle's own FP64
+    # rounding (it runs the definition in mpmath, not the oracle's code path).
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    cl = inputs.plummer(16, seed=5, imf="kroupa")
+    eps = 1e-3
+    acc, jerk, pot = oracle.force(cl.pos, cl.vel, cl.mass, eps)
+    P = [[mp.mpf(float(x)) for x in row] for row in cl.pos]
+    V = [[mp.mpf(float(x)) for x in row] for row in cl.vel]
+    Mm = [mp.mpf(float(x)) for x in cl.mass]
+    e2 = mp.mpf(eps) ** 2
+    for i in range(16):
+        a = [mp.mpf(0)] * 3
+        jk = [mp.mpf(0)] * 3
+        ph = mp.mpf(0)
+        ca = cj = mp.mpf(0)            # sums of |terms| (the conditioning)
+        for j in range(16):
+            if j == i:
+                continue
+            d = [P[j][c] - P[i][c] for c in range(3)]
+            w = [V[j][c] - V[i][c] for c in range(3)]
+            s = mp.sqrt(sum(x * x for x in d) + e2)
+            dw = sum(d[c] * w[c] for c in range(3))
+            for c in range(3):
+                ta = Mm[j] * d[c] / s ** 3
+                tj = Mm[j] * (w[c] / s ** 3 - 3 * dw * d[c] / s ** 5)
+                a[c] += ta
+                jk[c] += tj
+                ca += abs(ta)
+                cj += abs(tj)
+            ph -= Mm[j] / s
+        ref_a = np.array([float(x) for x in a])
+        ref_j = np.array([float(x) for x in jk])
+        # each FP64 term carries a few ulps; compensated summation adds ~1 ulp
+        assert np.abs(acc[i] - ref_a).max() <= 1e-15 * float(ca)
+        assert np.abs(jerk[i] - ref_j).max() <= 1e-15 * float(cj)
+        assert abs(pot[i] - float(ph)) <= 4e-16 * abs(float(ph))
+
+
+def test_force_subset_equals_full():
+    cl = inputs.plummer(100, seed=2)
+    a, j, p = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)
+    idx = np.array([99, 3, 50])
+    a2, j2, p2 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2, idx=idx)
+    assert np.array_equal(a2, a[idx]) and np.array_equal(j2, j[idx])
+    assert np.array_equal(p2, p[idx])
+    with pytest.raises(ValueError):
+        oracle.force(cl.pos, cl.vel, cl.mass, 1e-2, idx=[100])
+
+
+# --------------------------------------------------------------- energy ---
+
+def test_energy_closed_forms():
+    # softened pair energy at d = 3, eps = 4: -G m1 m2 / 5 exactly
+    ek, ep = oracle.energy(np.array([[0, 0, 0], [0, 3.0, 0]]),
+                           np.array([[1.0, 0, 0], [0, 0, 2.0]]),
+                           np.array([2.0, 5.0]), eps=4.0)
+    assert ep == pytest.approx(-2.0, rel=1e-15)
+    assert ek == pytest.approx(0.5 * 2 * 1 + 0.5 * 5 * 4, rel=1e-15)
+    # circular orbit: virial 2K = -W and E = -G m1 m2 / (2 r)
+    m1, m2, r = 0.7, 0.3, 1.7
+    M = m1 + m2
+    w = math.sqrt(M / r ** 3)
+    pos = np.array([[-m2 / M * r, 0, 0], [m1 / M * r, 0, 0]])
+    vel = np.array([[0, -m2 / M * r * w, 0], [0, m1 / M * r * w, 0]])
+    ek, ep = oracle.energy(pos, vel, np.array([m1, m2]), eps=0.0)
+    assert 2 * ek == pytest.approx(-ep, rel=1e-14)
+    assert ek + ep == pytest.approx(-m1 * m2 / (2 * r), rel=1e-14)
+    L, P = oracle.momenta(pos, vel, np.array([m1, m2]))
+    mu = m1 * m2 / M
+    assert L[2] == pytest.approx(mu * r * r * w, rel=1e-14)
+    np.testing.assert_allclose(P, 0.0, atol=1e-16)
+
+
+def test_potential_energy_is_half_sum_m_phi():
+    cl = inputs.plummer(200, seed=4, imf="kroupa")
+    _, _, pot = oracle.force(cl.pos, cl.vel, cl.mass, 1e-3)
+    _, ep = oracle.energy(cl.pos, cl.vel, cl.mass, 1e-3)
+    assert ep == pytest.approx(0.5 * np.dot(cl.mass, pot), rel=1e-13)
+
+
+# ------------------------------------------------------------ integrator ---
+
+def test_predictor_exact_for_constant_jerk_motion():
+    rng = np.random.default_rng(0)
+    x, v, a, j = (rng.normal(size=(5, 3)) for _ in range(4))
+    tau = np.array([0.0, 0.1, -0.2, 1.5, 0.03125])
+    xp, vp = oracle.predict(x, v, a, j, tau)
+    t = tau[:, None]
+    np.testing.assert_allclose(xp, x + v * t + a * t ** 2 / 2 + j * t ** 3 / 6, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(vp, v + a * t + j * t ** 2 / 2, rtol=1e-14, atol=1e-14)
+
+
+def test_corrector_recovers_quintic_trajectory():
+    # If a(t) is exactly a cubic, a = a0 + j0 t + s t^2/2 + c t^3/6, the
+    # two-point Hermite fit recovers s and c, and the corrected state is the
+    # exact x(tau), v(tau) of that motion.
+    rng = np.random.default_rng(1)
+    m = 4
+    x0, v0, a0, j0, s, c = (rng.normal(size=(m, 3)) for _ in range(6))
+    tau = np.array([0.5, 0.125, 1.0, 0.015625])
+    t = tau[:, None]
+    a1 = a0 + j0 * t + s * t ** 2 / 2 + c * t ** 3 / 6
+    j1 = j0 + s * t + c * t ** 2 / 2
+    xp, vp = oracle.predict(x0, v0, a0, j0, tau)
+    x1, v1, a2e, a3e = oracle.correct(tau, xp, vp, a0, j0, a1, j1)
+    x_ex = x0 + v0 * t + a0 * t ** 2 / 2 + j0 * t ** 3 / 6 + s * t ** 4 / 24 + c * t ** 5 / 120
+    v_ex = v0 + a0 * t + j0 * t ** 2 / 2 + s * t ** 3 / 6 + c * t ** 4 / 24
+    np.testing.assert_allclose(x1, x_ex, rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(v1, v_ex, rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(a3e, c, rtol=1e-8, atol=1e-8)
+    np.testing.assert_allclose(a2e, s + c * t, rtol=1e-9, atol=1e-9)
+
+
+def test_aarseth_dt_circular_orbit():
+    # uniform circular motion: |a| = w^2 r, |j| = w^3 r, |a2| = w^4 r,
+    # |a3| = w^5 r, so the criterion gives dt = sqrt(eta) / w.
+    w, r, eta = 3.0, 0.4, 0.01
+    ang = 0.3
+    u = np.array([math.cos(ang), math.sin(ang), 0.0])
+    p = np.array([-math.sin(ang), math.cos(ang), 0.0])
+    dt = oracle.aarseth_dt(-w ** 2 * r * u, -w ** 3 * r * p, w ** 4 * r * u, w ** 5 * r * p, eta)
+    assert dt == pytest.approx(math.sqrt(eta) / w, rel=1e-14)
+    assert oracle.aarseth_dt(u, np.zeros(3), np.zeros(3), np.zeros(3), eta) == math.inf
+    assert oracle.initial_dt(2 * u, 8 * p, 0.01) == pytest.approx(0.0025, rel=1e-15)
+
+
+def test_level_rules():
+    T = 40
+    # largest power of two not above dt_crit
+    assert oracle.level(0.3, -1, 0, T, 0, 30) == 2
+    assert oracle.level(0.25, -1, 0, T, 0, 30) == 2
+    assert oracle.level(0.2499999, -1, 0, T, 0, 30) == 3
+    assert oracle.level(2.0 ** -20 * 1.5, -1, 0, T, 0, 30) == 20
+    # clamps
+    assert oracle.level(1e-30, -1, 0, T, 3, 20) == 20
+    assert oracle.level(100.0, -1, 0, T, 3, 20) == 3
+    assert oracle.level(math.inf, -1, 0, T, 3, 20) == 3
+    assert oracle.level(0.0, -1, 0, T, 3, 20) == 20
+    # shrinking is always allowed, to any depth
+    assert oracle.level(2.0 ** -9, 5, 3 << (T - 5), T, 0, 30) == 9
+    # growing: one doubling at most, and only on a commensurate time
+    t_ok = 4 << (T - 5)        # multiple of 2^-4
+    t_bad = 3 << (T - 5)       # odd multiple of 2^-5
+    assert oracle.level(0.9, 5, t_ok, T, 0, 30) == 4
+    assert oracle.level(0.9, 5, t_bad, T, 0, 30) == 5
+    assert oracle.level(5.0, 0, 0, T, 0, 30) == 0     # already the largest step
+    assert oracle.level(0.9, 0, 0, T, 0, 30) == 1     # 0.5 <= 0.9 < 1: shrink
+
+
+def _kepler_state(a, e, M_tot, t, phase0=0.0):
+    """Relative position/velocity of a Kepler orbit at time t (periapsis at 0)."""
+    n = math.sqrt(M_tot / a ** 3)
+    Mn = n * t + phase0
+    E = Mn
+    for _ in range(100):
+        E = E - (E - e * math.sin(E) - Mn) / (1 - e * math.cos(E))
+    r = a * (1 - e * math.cos(E))
+    x = np.array([a * (math.cos(E) - e), a * math.sqrt(1 - e * e) * math.sin(E), 0.0])
+    v = np.array([-a * a * n * math.sin(E) / r, a * a * n * math.sqrt(1 - e * e) * math.cos(E) / r, 0.0])
+    return x, v
+
+
+def _kepler_run(level, e=0.5, t_end=1.0):
+    # period 1 time unit: a = 1, G M = 4 pi^2
+    M = 4 * math.pi ** 2
+    m1, m2 = 0.6 * M, 0.4 * M
+    x, v = _kepler_state(1.0, e, M, 0.0)
+    pos = np.array([-m2 / M * x, m1 / M * x])
+    vel = np.array([-m2 / M * v, m1 / M * v])
+    st = oracle.State(pos, vel, np.array([m1, m2]), eps=0.0, tick_exp=40,
+                      lmin=level, lmax=level)
+    nsteps = int(round(t_end * 2 ** level))
+    for _ in range(nsteps):
+        st.block_step()
+    xr, vr = _kepler_state(1.0, e, M, t_end)
+    rel = st.pos[1] - st.pos[0]
+    return np.linalg.norm(rel - xr), st
+
+
+def test_hermite4_kepler_fourth_order():
+    # Closed-form Kepler orbit (e = 0.5, one period): the Hermite scheme is
+    # 4th order (Sec. 2 item 1), so halving dt cuts the error by ~2^4.
+    errs = [_kepler_run(L)[0] for L in (8, 9, 10)]
+    assert errs[0] < 1e-4
+    for a, b in zip(errs, errs[1:]):
+        assert 12.0 < a / b < 20.0, errs
+
+
+def test_hermite4_kepler_mid_orbit_and_conservation():
+    err, st = _kepler_run(10, e=0.3, t_end=0.375)
+    assert err < 1e-8
+    ek, ep = oracle.energy(st.pos, st.vel, st.mass, 0.0)
+    # Kepler energy -G m1 m2 / (2a), a = 1; 4th-order truncation error only
+    assert ek + ep == pytest.approx(-st.mass[0] * st.mass[1] / 2.0, rel=1e-8)
+    assert st.time() == 0.375
+
+
+def test_block_step_equals_shared_step_composition():
+    # With every particle on one level the block step is one shared Hermite
+    # step; compose it from the primitive predictor / force / corrector.
+    cl = inputs.plummer(24, seed=9)
+    eps, L = 1e-2, 7
+    st = oracle.State(cl.pos, cl.vel, cl.mass, eps=eps, lmin=L, lmax=L)
+    x, v, a, j = st.pos.copy(), st.vel.copy(), st.acc.copy(), st.jerk.copy()
+    for _ in range(3):
+        tau = np.full(24, 2.0 ** -L)
+        xp, vp = oracle.predict(x, v, a, j, tau)
+        a1, j1, _ = oracle.force(xp, vp, cl.mass, eps)
+        x, v, _, _ = oracle.correct(tau, xp, vp, a, j, a1, j1)
+        a, j = a1, j1
+        t_next, act, _ = st.block_step()
+        assert len(act) == 24
+    assert np.array_equal(st.pos, x) and np.array_equal(st.vel, v)
+    assert np.array_equal(st.acc, a) and np.array_equal(st.jerk, j)
+    assert t_next == 3 << (40 - L)
+
+
+def test_block_step_invariants_and_conservation():
+    cl = inputs.plummer(64, seed=1)
+    eps = 1e-2
+    st = oracle.State(cl.pos, cl.vel, cl.mass, eps=eps, eta=0.02, lmin=3, lmax=16)
+    e0 = sum(oracle.energy(st.pos, st.vel, st.mass, eps))
+    L0, P0 = oracle.momenta(st.pos, st.vel, st.mass)
+    T = st.tick_exp
+    t_prev = 0
+    levels_seen = set()
+    while True:
+        due = st.t + (np.int64(1) << (T - st.level.astype(np.int64)))
+        t_next, act, _ = st.block_step()
+        assert t_next == due.min() and t_next > t_prev
+        assert np.array_equal(act, np.flatnonzero(due == t_next))
+        assert np.all(st.t[act] == t_next)
+        dt = np.int64(1) << (T - st.level.astype(np.int64))
+        assert np.all(st.t % dt == 0)               # commensurate times
+        assert st.level.min() >= 3 and st.level.max() <= 16
+        levels_seen.update(st.level.tolist())
+        t_prev = t_next
+        if t_next == 1 << (T - 3):                  # everybody synchronised
+            assert np.all(st.t == t_next)
+            break
+    assert len(levels_seen) > 1                     # really a block hierarchy
+    e1 = sum(oracle.energy(st.pos, st.vel, st.mass, eps))
+    L1, P1 = oracle.momenta(st.pos, st.vel, st.mass)
+    assert abs((e1 - e0) / e0) < 1e-6
+    # with individual steps the pair forces act at different times, so L and
+    # P are conserved only to truncation level (scale: sum m |v| ~ 0.7)
+    np.testing.assert_allclose(L1, L0, atol=1e-7)
+    np.testing.assert_allclose(P1, P0, atol=1e-7)
