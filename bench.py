@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark: pair-interactions/s of the direct-summation Hermite-4 step on GB300.
+
+Workload (N = 2^20 by default): a Plummer sphere with Kroupa-IMF masses
+(0.1-100, renormalised to M = 1), eps = 1e-4, Henon units, seeded synthetic
+initial conditions.  One step = one block time step of the whole hot path
+(next block time, active compaction, prediction of all N sources, force on the
+active set, i-split reduction, Hermite correction) with every particle on the
+same level, i.e. active fraction 1 (m = N): m * N pair interactions per step.
+
+Reported (one JSON line from rank 0):
+  value      interactions/s over the timed steps, device time (CUDA events on
+             the library's stream), L2 flushed between steps, max over ranks;
+  e2e        the same through the C ABI with pinned HOST buffers: state copied
+             in, one block step, state copied out, every step;
+  roofline   the mixed force kernel at 38 flops per interaction against the
+             FP32 peak 152 SMs x 128 lanes x 2 flops x 2.070 GHz;
+  sweep      nb_force alone at active fractions 2^-10 .. 1 (mixed) and
+             2^-10 .. 2^-6 (FP64), with error vs FP64 and vs the oracle;
+  cpu_baseline  the FP64 CPU oracle on the host cores, on a sample of targets.
+Multi-GPU (torchrun): every rank integrates its own independent cluster
+(seed = rank), no data-path collective; value sums the ranks' interactions.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_INTERACTION = 38          # acceleration + jerk convention
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+METRIC = "pair-interactions/s (and % FP32 peak) at N=2^20, mixed vs FP64, at stated error"
+UNIT = "pair-interactions/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=1 << 20)
+    p.add_argument("--level", type=int, default=10, help="shared step 2^-level")
+    p.add_argument("--no-sweep", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def workload_config(n):
+    return {"workload": f"Plummer N={n} Kroupa IMF 0.1-100 (M=1), eps=1e-4, Henon units; "
+                        "one Hermite-4 block step per step with all particles active "
+                        "(active fraction 1, shared level)",
+            "N": n, "eps": 1e-4, "imf": "kroupa", "active_fraction": 1.0,
+            "precision": "mixed: FP32 pair arithmetic on double-single separations, "
+                         "compensated FP32 per-tile sums combined in FP64, FP64 state",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def make_cluster(n, seed):
+    from paper_1411_5234_gb300 import inputs
+    return inputs.plummer(n, seed=seed, imf="kroupa")
+
+
+# ------------------------------------------------------------------ oracle --
+
+def oracle_sample(cl, seconds, seed=0):
+    """Time the FP64 CPU oracle on a random sample of targets vs all N sources."""
+    import oracle
+    from paper_1411_5234_gb300 import inputs
+    n = cl.n
+    probe = inputs.random_active(n, 128, seed=seed + 1).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=probe)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = 128 * n / dt
+    nt = int(min(max(rate * seconds / n, 128), n))
+    idx = inputs.random_active(n, nt, seed=seed + 2).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx)
+    dt = time.perf_counter() - t0
+    return {"value": nt * n / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{nt} random targets x all {n} sources (acc+jerk+pot, FP64, "
+                      f"Neumaier sums), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm (bounded samples of the same workload)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1411_5234_gb300 import inputs
+    cl = make_cluster(args.n, 0)
+    # size each step to ~10 s of CPU work
+    probe = inputs.random_active(cl.n, 16, seed=99).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=probe)
+    rate = 16 * cl.n / max(time.perf_counter() - t0, 1e-6)
+    nt = int(min(max(rate * 10.0 / cl.n, 16), cl.n))
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = inputs.random_active(cl.n, nt, seed=s).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * nt * cl.n / tot
+    cfg = workload_config(args.n)
+    cfg["reference_sample"] = f"{nt} random targets x all {cl.n} sources per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{nt} random targets x {cl.n} sources per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.rows = []
+        self.proc = None
+        self.device_id = device_id
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        pw = [float(r[2]) for r in self.rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(self.rows), "reasons": reasons}
+
+
+def traffic_from_profile(kernel_file):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (same sha256), else None."""
+    path = os.path.join(ROOT, "profiles", "force_mixed_n1048576.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = open(kernel_file, "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha256:\s*([0-9a-f]+)", text)
+    if m and m.group(2) == sha:
+        return float(m.group(1))
+    return None
+
+
+# ------------------------------------------------------------------- main ---
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1411_5234_gb300 import inputs, nbody
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    n = args.n
+    cl = make_cluster(n, seed=rank)
+    L = args.level
+    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nbody.NB_MIXED,
+                    level_min=L, level_max=L, graph_steps=0)
+    stream = sim.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sim.profile(True)
+
+    def one_step():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            sim.step(1)
+            ev1.record(stream)
+        return ev0, ev1
+
+    for _ in range(args.warmup):
+        one_step()
+    stream.synchronize()
+    sim.profile_read()                      # drop warm-up launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    dev_id = local
+    try:
+        dev_id = str(torch.cuda.get_device_properties(local).uuid)
+        dev_id = dev_id if dev_id.startswith("GPU-") else f"GPU-{dev_id}"
+    except Exception:
+        pass
+    with ClockSampler(dev_id) as clk:
+        evs = [one_step() for _ in range(args.steps)]
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    force_ms, force_launches = sim.profile_read()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    assert sim.status() == nbody.NB_OK, nbody.strerror(sim.status())
+    inter_step = n * n
+    value = world * args.steps * inter_step / (total_ms * 1e-3)
+    launches_per_step = 8   # tmin, predict, scan, scatter, plan, force, reduce, correct
+
+    clocks = clk.summary()
+    force_avg_s = force_ms * 1e-3 / max(force_launches, 1)
+    achieved = FLOPS_PER_INTERACTION * inter_step / force_avg_s / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    kfile = os.path.join(ROOT, "paper_1411_5234_gb300", "csrc", "nb_force_mixed.cu")
+    traffic = traffic_from_profile(kfile)
+    roofline = {"bound": "alu", "kernel": "k_force_mixed", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "flops_per_interaction": FLOPS_PER_INTERACTION,
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz (max clock)",
+                "force_ms_per_launch": force_avg_s * 1e3,
+                "force_share_of_step": force_ms / max(total_ms, 1e-9) if world == 1 else None}
+    if clocks.get("sm_mhz"):
+        pk = SMS * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12
+        roofline["peak_at_sampled_clock"] = pk
+        roofline["frac_at_sampled_clock"] = achieved / pk
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(n), "roofline": roofline,
+            "clocks": clocks, "gpu_launches": launches_per_step * args.steps}
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    if not args.no_e2e:
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()
+        hp, hv, ha, hj = (pin((n, 3), torch.float64) for _ in range(4))
+        ht, hl = pin((n,), torch.int64), pin((n,), torch.int32)
+        sim.profile(False)
+        sim.get_state_into(hp, hv, ha, hj, ht, hl)
+        e2e_t = []
+        for k in range(args.warmup + args.steps):
+            if dist:
+                dist.barrier()
+            t0 = time.perf_counter()
+            sim.set_state(hp, hv, ha, hj, ht, hl)
+            sim.step(1)
+            sim.get_state_into(hp, hv, ha, hj, ht, hl)
+            if k >= args.warmup:
+                e2e_t.append(time.perf_counter() - t0)
+        tot = sum(e2e_t)
+        if dist:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        h2d = 4 * 24 * n + 8 * n + 4 * n
+        line["e2e"] = {"value": world * args.steps * inter_step / tot, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                       "api": "nb_set_state + nb_step_block + nb_get_state (pinned host)"}
+    sim.close()
+
+    # ---- nb_force sweep over the active fraction, mixed and FP64 ----
+    if not args.no_sweep and rank == 0:
+        line["sweep"] = sweep(nbody, inputs, torch, cl)
+    if not args.no_cpu and rank == 0 and world == 1:
+        line["cpu_baseline"] = oracle_sample(cl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def sweep(nbody, inputs, torch, cl):
+    n = cl.n
+    out = {"unit": UNIT, "timing": "force kernel via CUDA events (nb_profile), best of 3",
+           "mixed": [], "fp64": []}
+    sims = {}
+    for name, prec in (("mixed", nbody.NB_MIXED), ("fp64", nbody.NB_FP64)):
+        s = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=prec, graph_steps=0)
+        s.predict(0)
+        s.profile(True)
+        sims[name] = s
+    for name, kmin, kmax in (("mixed", 10, 0), ("fp64", 10, 6)):
+        s = sims[name]
+        for k in range(kmin, kmax - 1, -1):
+            m = n >> k
+            act = torch.as_tensor(inputs.random_active(n, m, seed=k), device="cuda")
+            acc = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+            jerk = torch.empty_like(acc)
+            s.force(act, acc, jerk, None, want_pot=False)
+            s.synchronize()
+            s.profile_read()
+            best = math.inf
+            for _ in range(3):
+                s.force(act, acc, jerk, None, want_pot=False)
+                ms, cnt = s.profile_read()
+                best = min(best, ms / max(cnt, 1))
+            rate = m * n / (best * 1e-3)
+            entry = {"active_fraction": f"2^-{k}", "m": m, "interactions_per_s": rate,
+                     "ms": best}
+            if name == "mixed":
+                entry["frac_fp32_peak"] = (FLOPS_PER_INTERACTION * rate
+                                           / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6))
+            out[name].append(entry)
+    # accuracy: mixed vs FP64 on 4096 targets; both vs the oracle on 64 targets
+    import oracle
+    idx = inputs.random_active(n, 4096, seed=123)
+    act = torch.as_tensor(idx, device="cuda")
+    res = {}
+    for name in ("mixed", "fp64"):
+        a, j, p = sims[name].force(act)
+        sims[name].synchronize()
+        res[name] = (a.cpu().numpy(), j.cpu().numpy(), p.cpu().numpy())
+    rel = lambda x, r: np.linalg.norm(x - r, axis=1) / np.linalg.norm(r, axis=1)
+    ea, ej = rel(res["mixed"][0], res["fp64"][0]), rel(res["mixed"][1], res["fp64"][1])
+    ep = np.abs(res["mixed"][2] / res["fp64"][2] - 1)
+    sub = np.arange(0, 4096, 64)
+    ra, rj, _ = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx[sub].astype(np.int64))
+    out["accuracy"] = {
+        "mixed_vs_fp64_4096_targets": {
+            "acc_rel_max": float(ea.max()), "acc_rel_median": float(np.median(ea)),
+            "acc_rel_p999": float(np.quantile(ea, 0.999)),
+            "jerk_rel_max": float(ej.max()), "jerk_rel_median": float(np.median(ej)),
+            "pot_rel_max": float(ep.max())},
+        "fp64_vs_oracle_64_targets": {
+            "acc_rel_max": float(rel(res["fp64"][0][sub], ra).max()),
+            "jerk_rel_max": float(rel(res["fp64"][1][sub], rj).max())},
+        "mixed_vs_oracle_64_targets": {
+            "acc_rel_max": float(rel(res["mixed"][0][sub], ra).max()),
+            "jerk_rel_max": float(rel(res["mixed"][1][sub], rj).max())}}
+    mx = {e["m"]: e["interactions_per_s"] for e in out["mixed"]}
+    out["mixed_over_fp64_speedup"] = {e["active_fraction"]: mx[e["m"]] / e["interactions_per_s"]
+                                      for e in out["fp64"]}
+    for s in sims.values():
+        s.close()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * nbody_gb300.h -- C ABI of libnbody_gb300.so: direct-summation N-body forces
+ * with a 4th-order Hermite block-time-step integrator on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * The library computes, for a set of "active" particles, the softened
+ * Newtonian acceleration, its time derivative (jerk) and the potential due to
+ * all N sources of the same cluster (Eq. 1 with the softening of Eq. 2), and
+ * drives it with the Hermite predictor-corrector (Sec. 2 item 1) on
+ * power-of-two block time steps (Sec. 2 item 2).  Several independent
+ * clusters may share one context (a batch); forces never cross clusters.
+ *
+ * Conventions
+ *   - Units: G is a parameter (default 1).  Softening eps >= 0; with eps == 0
+ *     two distinct particles at the same position give non-finite values.
+ *   - Particle i's acceleration sums j != i of its own cluster:
+ *       a_i    =  G sum m_j d / s^3,           d = r_j - r_i, s^2 = |d|^2 + eps^2
+ *       jerk_i =  G sum m_j (w / s^3 - 3 (d.w) d / s^5),    w = v_j - v_i
+ *       pot_i  = -G sum m_j / s
+ *   - Time is an integer number of ticks of 2^-tick_exp time units; a
+ *     particle on level L has the step dt = 2^-L time units.
+ *   - Host vectors are row-major (n, 3) doubles; device result vectors are
+ *     row-major (m, 3) doubles.
+ *
+ * Precision (nb_config.precision)
+ *   NB_FP64  : every operation in IEEE FP64.
+ *   NB_MIXED : the pair arithmetic in FP32 with double-single (hi + lo FP32)
+ *              positions so that the separation keeps FP64-like resolution
+ *              (Sec. 2 item 4: DP for distances and accumulation, the rest,
+ *              square roots included, in SP); sums over sources accumulated
+ *              with a compensated FP32 pair per tile and combined in FP64;
+ *              predictor, corrector, time, state and energy stay FP64.
+ *
+ * Memory ownership
+ *   All device memory is the caller's: nb_workspace_size() gives the bytes of
+ *   ONE device buffer that the caller allocates (e.g. a torch uint8 tensor)
+ *   and passes to nb_init(); it must stay allocated until nb_free().  The
+ *   library keeps a small host struct (nb_ctx), never allocates device memory
+ *   itself, and keeps no host pointer after a call returns.
+ *
+ * Streams and synchronisation
+ *   Every call runs on the stream given to nb_init() (NULL = legacy default
+ *   stream).  nb_predict, nb_force, nb_correct and nb_step_block only enqueue
+ *   work and return; nb_init, nb_energy, nb_get_state, nb_set_state,
+ *   nb_stats and nb_status synchronise that stream.
+ *
+ * Errors
+ *   Every int-returning call returns NB_OK or a positive NB_E* code and never
+ *   aborts, exits or traps.  Argument errors are reported immediately.
+ *   Errors found on the device (bad active list, non-finite results, a device
+ *   wait that gave up) set a sticky status word in the workspace; the
+ *   synchronising calls return it, and nb_status() reads it.
+ *
+ * Thread safety: a context is used by one host thread at a time.
+ */
+#ifndef NBODY_GB300_H
+#define NBODY_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define NB_OK          0
+#define NB_EINVAL      1   /* bad argument (NULL, size, range, order)        */
+#define NB_ENOMEM      2   /* workspace smaller than nb_workspace_size()     */
+#define NB_ECUDA       3   /* a CUDA runtime call failed                     */
+#define NB_ETIMEOUT    4   /* a device-side wait gave up (bounded spin)      */
+#define NB_ENONFINITE  5   /* NaN/Inf produced by the corrector              */
+#define NB_ESTATE      6   /* call not valid in the context's current state  */
+
+typedef struct nb_ctx nb_ctx;
+
+typedef enum { NB_FP64 = 0, NB_MIXED = 1 } nb_precision;
+
+typedef struct {
+    double  G;          /* gravitational constant (Eq. 1)                      */
+    double  eps;        /* softening length (Eq. 2), >= 0                      */
+    double  eta;        /* accuracy parameter of the step criterion            */
+    double  eta_start;  /* accuracy parameter of the initial step              */
+    int32_t level_min;  /* largest step  = 2^-level_min, 0 <= level_min        */
+    int32_t level_max;  /* smallest step = 2^-level_max, level_min <= level_max */
+    int32_t tick_exp;   /* one tick = 2^-tick_exp time units, level_max <= tick_exp <= 60 */
+    int32_t precision;  /* nb_precision                                        */
+    int32_t bfactor;    /* i-split factor B: 0 = chosen per step by the plan   */
+    int32_t graph_steps;/* block steps captured per CUDA graph (0 = no graph)  */
+    int32_t reserved[2];
+} nb_config;
+
+/* Defaults: G = 1, eps = 1e-4, eta = 0.01, eta_start = 0.01, level_min = 0,
+ * level_max = 30, tick_exp = 40, NB_MIXED, bfactor = 0, graph_steps = 16. */
+void nb_default_config(nb_config *cfg);
+
+/* Bytes of the device workspace for n_total particles in n_clusters clusters
+ * (n_clusters >= 1; every cluster holds >= 1 particle).  NB_EINVAL on bad
+ * sizes or config. */
+int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config *cfg,
+                      size_t *bytes);
+
+/* Create a context.  offsets (host, n_clusters + 1, offsets[0] = 0, strictly
+ * increasing, offsets[n_clusters] = n_total) delimit the clusters; mass (n),
+ * pos and vel (n x 3) are host arrays copied during the call.  workspace is a
+ * device pointer (256-byte aligned) of at least nb_workspace_size() bytes.
+ * stream is a cudaStream_t (or NULL).  Computes the acceleration and jerk of
+ * every particle at t = 0 (one force evaluation), sets every time to 0 and
+ * assigns the first levels from eta_start |a| / |jerk| (clamped to
+ * [level_min, level_max]).  Synchronises the stream. */
+int nb_init(nb_ctx **out, const nb_config *cfg, int32_t n_clusters,
+            const int64_t *offsets, const double *mass, const double *pos,
+            const double *vel, void *workspace, size_t workspace_bytes,
+            void *stream);
+
+/* Release the host context (the workspace stays the caller's). */
+void nb_free(nb_ctx *ctx);
+
+/* Predict EVERY particle to time t_ticks with the Taylor predictor of the
+ * Hermite scheme (Sec. 2 items 1 and 2) and store the result as the source
+ * set used by nb_force.  Asynchronous. */
+int nb_predict(nb_ctx *ctx, int64_t t_ticks);
+
+/* Acceleration, jerk and potential (Eq. 1, Eq. 2) of the m particles listed in
+ * active_idx (device int32, m entries, global particle indices, strictly
+ * ascending) from the predicted sources of their own cluster (the last
+ * nb_predict).  acc and jerk: device (m x 3) doubles; pot: device m doubles
+ * or NULL.  Row k of the outputs belongs to active_idx[k].  m == 0 is a
+ * no-op.  Asynchronous; an unsorted or out-of-range list sets the sticky
+ * status to NB_EINVAL and the rows of the offending entries are left
+ * unwritten. */
+int nb_force(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
+             double *jerk, double *pot);
+
+/* Hermite correction (Sec. 2 item 1) of the m particles in active_idx
+ * (device, as for nb_force) from their own times to t_ticks, given their new
+ * acceleration and jerk evaluated at the predicted state (device m x 3, as
+ * written by nb_force).  Sets each particle's time to t_ticks and a new level
+ * from the step criterion.  Asynchronous. */
+int nb_correct(nb_ctx *ctx, int64_t t_ticks, const int32_t *active_idx,
+               int64_t m, const double *acc, const double *jerk);
+
+/* Run n_steps block steps (Sec. 2 item 2).  In one block step EVERY cluster
+ * whose time is below the end time (nb_set_end_time) independently takes its
+ * next block time t_next = min_i (t_i + dt_i), predicts all its particles to
+ * t_next, evaluates the force on its active set {i : t_i + dt_i = t_next}
+ * and corrects that set.  All sizes live on the device, so the sequence is
+ * launched without host synchronisation (CUDA graphs of graph_steps steps).
+ * Asynchronous. */
+int nb_step_block(nb_ctx *ctx, int64_t n_steps);
+
+/* Clusters stop stepping once their time reaches t_end_ticks (a multiple of
+ * 2^-level_min time units keeps every particle synchronised there).
+ * Default: no end time. */
+int nb_set_end_time(nb_ctx *ctx, int64_t t_end_ticks);
+
+/* FP64 kinetic and softened potential energy of cluster `cluster` (-1: all
+ * clusters summed), with every particle predicted to its cluster's current
+ * block time.  Host outputs; synchronises. */
+int nb_energy(nb_ctx *ctx, int32_t cluster, double *ekin, double *epot);
+
+/* Copy the state to host arrays (any pointer may be NULL): pos, vel, acc,
+ * jerk (n x 3), t (n ticks), level (n).  The vectors are packed on the device
+ * and copied straight into the caller's arrays (pinned arrays copy at full
+ * host-link bandwidth).  Synchronises. */
+int nb_get_state(nb_ctx *ctx, double *pos, double *vel, double *acc,
+                 double *jerk, int64_t *t, int32_t *level);
+
+/* Overwrite the state from host arrays (all six required; masses keep their
+ * nb_init values).  Levels must lie in [level_min, level_max] and each time
+ * must be a multiple of its step.  Synchronises. */
+int nb_set_state(nb_ctx *ctx, const double *pos, const double *vel,
+                 const double *acc, const double *jerk, const int64_t *t,
+                 const int32_t *level);
+
+/* Counters since nb_init (host outputs, any may be NULL): block steps taken,
+ * pair interactions evaluated (sum over force evaluations of m x N_cluster),
+ * smallest and largest cluster time in ticks.  Synchronises. */
+int nb_stats(nb_ctx *ctx, int64_t *block_steps, int64_t *interactions,
+             int64_t *t_min, int64_t *t_max);
+
+/* Force-kernel timing.  While enabled, CUDA events bracket every launch of
+ * the force kernel on the context's stream (block steps are then launched
+ * directly instead of through CUDA graphs).  nb_profile_read synchronises and
+ * returns the summed device milliseconds of those launches and their count
+ * since the previous read (either pointer may be NULL). */
+int nb_profile_enable(nb_ctx *ctx, int enable);
+int nb_profile_read(nb_ctx *ctx, double *force_ms, int64_t *launches);
+
+/* Sticky device status (NB_OK or an NB_E* code); synchronises. */
+int nb_status(nb_ctx *ctx);
+
+/* Clear the sticky device status. */
+int nb_clear_status(nb_ctx *ctx);
+
+/* Text for a status code (static storage). */
+const char *nb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_GB300_H */

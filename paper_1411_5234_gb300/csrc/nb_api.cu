@@ -1,0 +1,666 @@
+// nb_api.cu -- the C ABI of libnbody_gb300 (declared in include/nbody_gb300.h).
+//
+// Host side only: argument checks, workspace layout, and the enqueue order of
+// the kernels in nb_force_*.cu and nb_integrator.cu.  No device memory is
+// allocated here; the caller's workspace is carved into the arrays below.
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/nbody_gb300.h"
+#include "nb_integrator.cuh"
+
+using namespace nb;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kEnergyBlocks = 304;
+
+struct Layout {
+  size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
+      src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, bfac, esum,
+      status, counters, t_end, total;
+  int64_t S, part_items;
+};
+
+size_t take(size_t& cur, size_t bytes) {
+  const size_t o = cur;
+  cur += (bytes + kAlign - 1) / kAlign * kAlign;
+  return o;
+}
+
+Layout make_layout(int64_t N, int32_t K, int64_t S) {
+  Layout L{};
+  L.S = S;
+  const int64_t nitile = ceil_div64(N, kF64NI) + K;
+  L.part_items = 2 * nitile > 2048 ? 2 * nitile : 2048;
+  const size_t ni_max = kMixNI > kF64NI ? kMixNI : kF64NI;
+  size_t c = 0;
+  L.pos = take(c, 32 * N);
+  L.vel = take(c, 32 * N);
+  L.acc = take(c, 32 * N);
+  L.jerk = take(c, 32 * N);
+  L.acc_new = take(c, 32 * N);
+  L.jerk_new = take(c, 32 * N);
+  L.t = take(c, 8 * N);
+  L.level = take(c, 4 * N);
+  L.cid = take(c, 4 * N);
+  L.active = take(c, 4 * N);
+  L.src_mix = take(c, 40 * S);
+  L.src64_pos = take(c, 32 * S);
+  L.src64_vel = take(c, 32 * S);
+  L.partials = take(c, (size_t)L.part_items * kPartialComps * ni_max * 8);
+  L.blk_count = take(c, 4 * ((size_t)scan_blocks(N) + 1));
+  L.off = take(c, 8 * ((size_t)K + 1));
+  L.soff = take(c, 8 * ((size_t)K + 1));
+  L.t_cur = take(c, 8 * (size_t)K);
+  L.t_min = take(c, 8 * (size_t)K);
+  L.act_off = take(c, 4 * ((size_t)K + 1));
+  L.item_off = take(c, 4 * ((size_t)K + 1));
+  L.bfac = take(c, 4 * (size_t)K);
+  L.esum = take(c, 8 * (2 * (size_t)kEnergyBlocks + 2));
+  L.status = take(c, 4);
+  L.counters = take(c, 8 * 4);
+  L.t_end = take(c, 8);
+  L.total = c;
+  return L;
+}
+
+bool config_ok(const nb_config* c) {
+  if (!c) return false;
+  if (!std::isfinite(c->G) || !std::isfinite(c->eps) || c->eps < 0.0) return false;
+  if (!(c->eta > 0.0) || !std::isfinite(c->eta)) return false;
+  if (!(c->eta_start > 0.0) || !std::isfinite(c->eta_start)) return false;
+  if (c->tick_exp < 1 || c->tick_exp > kMaxTickExp) return false;
+  if (c->level_min < 0 || c->level_min > c->level_max || c->level_max > c->tick_exp) return false;
+  if (c->precision != NB_FP64 && c->precision != NB_MIXED) return false;
+  if (c->bfactor < 0 || c->graph_steps < 0) return false;
+  return true;
+}
+
+int64_t slots_of(const int64_t* off, int32_t K) {
+  int64_t S = 0;
+  for (int32_t k = 0; k < K; ++k) S += round_up64(off[k + 1] - off[k], 4);
+  return S;
+}
+
+}  // namespace
+
+struct nb_ctx {
+  nb_config cfg{};
+  Dev d;
+  Layout L{};
+  cudaStream_t st = nullptr;
+  int grid_mix = 0, grid_f64 = 0;
+  std::vector<int64_t> off_host;
+  std::vector<double> mass_host;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  bool graph_broken = false;
+  // force-kernel timing (nb_profile_enable)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  double prof_ms = 0.0;
+  int64_t prof_launches = 0;
+};
+
+namespace {
+
+#define NB_TRY(x)                              \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return NB_ECUDA;    \
+  } while (0)
+
+bool is_mixed(const nb_ctx* c) { return c->cfg.precision == NB_MIXED; }
+
+ForceArgs force_args(nb_ctx* c, const int32_t* active, double* acc, int sa, double* jerk, int sj,
+                     double* pot, int sp, bool f64_sources) {
+  ForceArgs a{};
+  a.off = c->d.off;
+  a.soff = c->d.soff;
+  a.active = active;
+  a.act_off = c->d.act_off;
+  a.item_off = c->d.item_off;
+  a.bfac = c->d.bfac;
+  a.K = c->d.K;
+  if (f64_sources) {
+    a.src_a = c->d.src64_pos;
+    a.src_b = c->d.src64_vel;
+  } else {
+    a.src_a = c->d.src_mix;
+    a.src_b = nullptr;
+  }
+  a.out_acc = acc;
+  a.sa = sa;
+  a.out_jerk = jerk;
+  a.sj = sj;
+  a.out_pot = pot;
+  a.sp = sp;
+  a.partials = c->d.partials;
+  a.G = c->cfg.G;
+  a.eps2 = c->cfg.eps * c->cfg.eps;
+  a.status = c->d.status;
+  return a;
+}
+
+PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count) {
+  PlanArgs p{};
+  p.NI = f64 ? kF64NI : kMixNI;
+  p.JT = f64 ? kF64JT : kMixJT;
+  p.grid = f64 ? c->grid_f64 : c->grid_mix;
+  p.forced_b = c->cfg.bfactor;
+  p.part_items = c->L.part_items;
+  p.step_mode = step_mode;
+  p.count = count;
+  return p;
+}
+
+// Fold finished event pairs into the running total (blocking when `all`).
+cudaError_t prof_collect(nb_ctx* c, bool all) {
+  size_t k = 0;
+  for (; k < c->ev_pending.size(); ++k) {
+    auto& p = c->ev_pending[k];
+    if (all) {
+      cudaError_t e = cudaEventSynchronize(p.second);
+      if (e != cudaSuccess) return e;
+    } else if (cudaEventQuery(p.second) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, p.first, p.second);
+    if (e != cudaSuccess) return e;
+    c->prof_ms += ms;
+    c->prof_launches += 1;
+    c->ev_free.push_back(p.first);
+    c->ev_free.push_back(p.second);
+  }
+  c->ev_pending.erase(c->ev_pending.begin(), c->ev_pending.begin() + k);
+  return cudaSuccess;
+}
+
+cudaError_t prof_events(nb_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
+  if (c->ev_pending.size() >= 512) {
+    cudaError_t e = prof_collect(c, true);
+    if (e != cudaSuccess) return e;
+  }
+  cudaEvent_t x[2];
+  for (int q = 0; q < 2; ++q) {
+    if (!c->ev_free.empty()) {
+      x[q] = c->ev_free.back();
+      c->ev_free.pop_back();
+    } else {
+      cudaError_t e = cudaEventCreate(&x[q]);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  *ev = {x[0], x[1]};
+  return cudaSuccess;
+}
+
+// plan + force + partial reduce on the active list already described by
+// act_off (and `active`, or the identity when null).
+cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, double* acc, int sa, double* jerk,
+                          int sj, double* pot, int sp, bool f64, int step_mode, int count,
+                          bool pot_only, int64_t m_bound) {
+  cudaError_t e = launch_plan(c->d, plan_args(c, f64, step_mode, count), c->st);
+  if (e != cudaSuccess) return e;
+  ForceArgs fa = force_args(c, active, acc, sa, jerk, sj, pot, sp, f64);
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (c->prof) {
+    e = prof_events(c, &ev);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev.first, c->st);
+    if (e != cudaSuccess) return e;
+  }
+  if (f64)
+    e = launch_force_fp64(fa, c->grid_f64, pot_only ? kF64PotOnly : kF64Full, c->st);
+  else
+    e = launch_force_mixed(fa, c->grid_mix, pot != nullptr, c->st);
+  if (e != cudaSuccess) return e;
+  if (c->prof) {
+    e = cudaEventRecord(ev.second, c->st);
+    if (e != cudaSuccess) return e;
+    c->ev_pending.push_back(ev);
+  }
+  return launch_reduce(fa, f64 ? kF64NI : kMixNI, !pot_only, m_bound, c->st);
+}
+
+cudaError_t enqueue_block_step(nb_ctx* c) {
+  const int T = c->cfg.tick_exp;
+  const bool f64 = !is_mixed(c);
+  cudaError_t e = launch_tmin(c->d, T, c->st);
+  if (e != cudaSuccess) return e;
+  e = launch_predict(c->d, c->d.t_min, 0, T, !f64, f64, true, c->st);
+  if (e != cudaSuccess) return e;
+  e = launch_compact(c->d, T, c->st);
+  if (e != cudaSuccess) return e;
+  double* an = reinterpret_cast<double*>(c->d.acc_new);
+  double* jn = reinterpret_cast<double*>(c->d.jerk_new);
+  e = enqueue_force(c, c->d.active, an, 4, jn, 4, an + 3, 4, f64, 1, 1, false, c->d.N);
+  if (e != cudaSuccess) return e;
+  CorrectArgs ca{};
+  ca.active = c->d.active;
+  ca.count_dev = c->d.act_off + c->d.K;
+  ca.acc = an;
+  ca.sa = 4;
+  ca.jerk = jn;
+  ca.sj = 4;
+  ca.pot = an + 3;
+  ca.sp = 4;
+  ca.t_tgt = c->d.t_cur;
+  ca.eta = c->cfg.eta;
+  ca.T = T;
+  ca.lmin = c->cfg.level_min;
+  ca.lmax = c->cfg.level_max;
+  return launch_correct(c->d, ca, c->d.N, c->st);
+}
+
+int sync_status(nb_ctx* c) {
+  uint32_t s = 0;
+  if (cudaMemcpyAsync(&s, c->d.status, sizeof s, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    return NB_ECUDA;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return NB_ECUDA;
+  if (s & kStatusTimeout) return NB_ETIMEOUT;
+  if (s & kStatusNonFinite) return NB_ENONFINITE;
+  if (s & kStatusInval) return NB_EINVAL;
+  return NB_OK;
+}
+
+bool finite_all(const double* x, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nb_default_config(nb_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->G = 1.0;
+  cfg->eps = 1e-4;
+  cfg->eta = 0.01;
+  cfg->eta_start = 0.01;
+  cfg->level_min = 0;
+  cfg->level_max = 30;
+  cfg->tick_exp = 40;
+  cfg->precision = NB_MIXED;
+  cfg->bfactor = 0;
+  cfg->graph_steps = 16;
+}
+
+int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config* cfg, size_t* bytes) {
+  if (!bytes || !config_ok(cfg) || n_clusters < 1 || n_total < n_clusters ||
+      n_total > (int64_t)INT32_MAX - 1024)
+    return NB_EINVAL;
+  // worst case of the slot padding: 3 pad slots per cluster
+  *bytes = make_layout(n_total, n_clusters, n_total + 3 * (int64_t)n_clusters).total;
+  return NB_OK;
+}
+
+int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_t* offsets,
+            const double* mass, const double* pos, const double* vel, void* workspace,
+            size_t workspace_bytes, void* stream) {
+  if (!out || !config_ok(cfg) || n_clusters < 1 || !offsets || !mass || !pos || !vel ||
+      !workspace)
+    return NB_EINVAL;
+  *out = nullptr;
+  if (offsets[0] != 0) return NB_EINVAL;
+  for (int32_t k = 0; k < n_clusters; ++k)
+    if (offsets[k + 1] <= offsets[k]) return NB_EINVAL;
+  const int64_t N = offsets[n_clusters];
+  if (N > (int64_t)INT32_MAX - 1024) return NB_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return NB_EINVAL;
+  if (!finite_all(mass, N) || !finite_all(pos, 3 * N) || !finite_all(vel, 3 * N)) return NB_EINVAL;
+  for (int64_t i = 0; i < N; ++i)
+    if (mass[i] < 0.0) return NB_EINVAL;
+  size_t need = 0;
+  if (nb_workspace_size(N, n_clusters, cfg, &need) != NB_OK) return NB_EINVAL;
+  if (workspace_bytes < need) return NB_ENOMEM;
+
+  nb_ctx* c = new nb_ctx();
+  c->cfg = *cfg;
+  c->st = static_cast<cudaStream_t>(stream);
+  c->off_host.assign(offsets, offsets + n_clusters + 1);
+  c->mass_host.assign(mass, mass + N);
+  const int64_t S = slots_of(offsets, n_clusters);
+  c->L = make_layout(N, n_clusters, S);
+  char* w = static_cast<char*>(workspace);
+  Dev& d = c->d;
+  d.N = N;
+  d.S = S;
+  d.K = n_clusters;
+  d.pos = reinterpret_cast<dbl4*>(w + c->L.pos);
+  d.vel = reinterpret_cast<dbl4*>(w + c->L.vel);
+  d.acc = reinterpret_cast<dbl4*>(w + c->L.acc);
+  d.jerk = reinterpret_cast<dbl4*>(w + c->L.jerk);
+  d.acc_new = reinterpret_cast<dbl4*>(w + c->L.acc_new);
+  d.jerk_new = reinterpret_cast<dbl4*>(w + c->L.jerk_new);
+  d.t = reinterpret_cast<int64_t*>(w + c->L.t);
+  d.level = reinterpret_cast<int32_t*>(w + c->L.level);
+  d.cid = reinterpret_cast<int32_t*>(w + c->L.cid);
+  d.active = reinterpret_cast<int32_t*>(w + c->L.active);
+  d.src_mix = reinterpret_cast<float4*>(w + c->L.src_mix);
+  d.src64_pos = reinterpret_cast<dbl4*>(w + c->L.src64_pos);
+  d.src64_vel = reinterpret_cast<dbl4*>(w + c->L.src64_vel);
+  d.partials = reinterpret_cast<double*>(w + c->L.partials);
+  d.part_items = c->L.part_items;
+  d.blk_count = reinterpret_cast<int32_t*>(w + c->L.blk_count);
+  d.off = reinterpret_cast<int64_t*>(w + c->L.off);
+  d.soff = reinterpret_cast<int64_t*>(w + c->L.soff);
+  d.t_cur = reinterpret_cast<int64_t*>(w + c->L.t_cur);
+  d.t_min = reinterpret_cast<int64_t*>(w + c->L.t_min);
+  d.act_off = reinterpret_cast<int32_t*>(w + c->L.act_off);
+  d.item_off = reinterpret_cast<int32_t*>(w + c->L.item_off);
+  d.bfac = reinterpret_cast<int32_t*>(w + c->L.bfac);
+  d.esum = reinterpret_cast<double*>(w + c->L.esum);
+  d.status = reinterpret_cast<uint32_t*>(w + c->L.status);
+  d.counters = reinterpret_cast<unsigned long long*>(w + c->L.counters);
+  d.t_end = reinterpret_cast<int64_t*>(w + c->L.t_end);
+
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return NB_ECUDA;
+  }
+  c->grid_mix = sms * force_mixed_ctas_per_sm();
+  c->grid_f64 = sms * force_fp64_ctas_per_sm();
+
+  // host staging of the initial state
+  std::vector<double> p4(4 * N), v4(4 * N, 0.0);
+  std::vector<int32_t> cid(N);
+  std::vector<int64_t> soff(n_clusters + 1, 0);
+  for (int32_t k = 0; k < n_clusters; ++k) {
+    soff[k + 1] = soff[k] + round_up64(offsets[k + 1] - offsets[k], 4);
+    for (int64_t i = offsets[k]; i < offsets[k + 1]; ++i) cid[i] = k;
+  }
+  for (int64_t i = 0; i < N; ++i) {
+    p4[4 * i] = pos[3 * i];
+    p4[4 * i + 1] = pos[3 * i + 1];
+    p4[4 * i + 2] = pos[3 * i + 2];
+    p4[4 * i + 3] = mass[i];
+    v4[4 * i] = vel[3 * i];
+    v4[4 * i + 1] = vel[3 * i + 1];
+    v4[4 * i + 2] = vel[3 * i + 2];
+  }
+  const int64_t big = LLONG_MAX;
+  int rc = NB_OK;
+  cudaStream_t st = c->st;
+  do {
+    if (cudaMemcpyAsync(d.pos, p4.data(), 32 * N, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(d.vel, v4.data(), 32 * N, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(d.cid, cid.data(), 4 * N, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(d.off, offsets, 8 * (n_clusters + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(d.soff, soff.data(), 8 * (n_clusters + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemsetAsync(d.acc, 0, 32 * N, st) || cudaMemsetAsync(d.jerk, 0, 32 * N, st) ||
+        cudaMemsetAsync(d.t, 0, 8 * N, st) || cudaMemsetAsync(d.level, 0, 4 * N, st) ||
+        cudaMemsetAsync(d.t_cur, 0, 8 * n_clusters, st) ||
+        cudaMemsetAsync(d.status, 0, 4, st) || cudaMemsetAsync(d.counters, 0, 32, st)) {
+      rc = NB_ECUDA;
+      break;
+    }
+    if (launch_fill_i64(d.t_min, n_clusters, big, st) || launch_fill_i64(d.t_end, 1, big, st) ||
+        launch_init_pads(d, st)) {
+      rc = NB_ECUDA;
+      break;
+    }
+    const bool f64 = !is_mixed(c);
+    double* an = reinterpret_cast<double*>(d.acc_new);
+    double* jn = reinterpret_cast<double*>(d.jerk_new);
+    if (launch_predict(d, nullptr, 0, cfg->tick_exp, !f64, f64, false, st) ||
+        launch_actoff_identity(d, st) ||
+        enqueue_force(c, nullptr, an, 4, jn, 4, an + 3, 4, f64, 0, 0, false, N) ||
+        launch_init_levels(d, cfg->eta_start, cfg->tick_exp, cfg->level_min, cfg->level_max, st)) {
+      rc = NB_ECUDA;
+      break;
+    }
+    rc = sync_status(c);
+  } while (false);
+  if (rc != NB_OK) {
+    cudaStreamSynchronize(st);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return NB_OK;
+}
+
+void nb_free(nb_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto& p : c->ev_pending) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  for (auto e : c->ev_free) cudaEventDestroy(e);
+  delete c;
+}
+
+int nb_predict(nb_ctx* c, int64_t t_ticks) {
+  if (!c || t_ticks < 0) return NB_EINVAL;
+  const bool f64 = !is_mixed(c);
+  NB_TRY(launch_predict(c->d, nullptr, t_ticks, c->cfg.tick_exp, !f64, f64, false, c->st));
+  return NB_OK;
+}
+
+int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, double* jerk,
+             double* pot) {
+  if (!c || m < 0 || m > c->d.N) return NB_EINVAL;
+  if (m == 0) return NB_OK;
+  if (!active_idx || !acc || !jerk) return NB_EINVAL;
+  const bool f64 = !is_mixed(c);
+  NB_TRY(launch_actoff_list(c->d, active_idx, m, c->st));
+  NB_TRY(enqueue_force(c, active_idx, acc, 3, jerk, 3, pot, 1, f64, 0, 1, false, m));
+  return NB_OK;
+}
+
+int nb_correct(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
+               const double* acc, const double* jerk) {
+  if (!c || m < 0 || m > c->d.N || t_ticks < 0) return NB_EINVAL;
+  if (m == 0) return NB_OK;
+  if (!active_idx || !acc || !jerk) return NB_EINVAL;
+  CorrectArgs ca{};
+  ca.active = active_idx;
+  ca.count_dev = nullptr;
+  ca.count_host = m;
+  ca.acc = acc;
+  ca.sa = 3;
+  ca.jerk = jerk;
+  ca.sj = 3;
+  ca.pot = nullptr;
+  ca.t_tgt = nullptr;
+  ca.t_fixed = t_ticks;
+  ca.eta = c->cfg.eta;
+  ca.T = c->cfg.tick_exp;
+  ca.lmin = c->cfg.level_min;
+  ca.lmax = c->cfg.level_max;
+  NB_TRY(launch_correct(c->d, ca, m, c->st));
+  return NB_OK;
+}
+
+int nb_step_block(nb_ctx* c, int64_t n_steps) {
+  if (!c || n_steps < 0) return NB_EINVAL;
+  const int G = c->cfg.graph_steps;
+  const bool graphs = G > 0 && c->st != nullptr && !c->graph_broken && !c->prof;
+  if (graphs && c->graph == nullptr && n_steps >= G) {
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      for (int s = 0; s < G && ok; ++s) ok = enqueue_block_step(c) == cudaSuccess;
+      const bool ended = cudaStreamEndCapture(c->st, &g) == cudaSuccess;
+      ok = ok && ended && cudaGraphInstantiate(&c->graph, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+    }
+    if (!ok) {
+      c->graph = nullptr;
+      c->graph_broken = true;  // fall back to direct launches of the same kernels
+      cudaGetLastError();
+    } else {
+      c->graph_len = G;
+    }
+  }
+  int64_t left = n_steps;
+  if (c->graph && !c->prof) {
+    while (left >= c->graph_len) {
+      NB_TRY(cudaGraphLaunch(c->graph, c->st));
+      left -= c->graph_len;
+    }
+  }
+  for (; left > 0; --left) NB_TRY(enqueue_block_step(c));
+  return NB_OK;
+}
+
+int nb_set_end_time(nb_ctx* c, int64_t t_end_ticks) {
+  if (!c || t_end_ticks < 0) return NB_EINVAL;
+  NB_TRY(launch_fill_i64(c->d.t_end, 1, t_end_ticks, c->st));
+  return NB_OK;
+}
+
+int nb_energy(nb_ctx* c, int32_t cluster, double* ekin, double* epot) {
+  if (!c || !ekin || !epot || cluster < -1 || cluster >= c->d.K) return NB_EINVAL;
+  Dev& d = c->d;
+  double* an = reinterpret_cast<double*>(d.acc_new);
+  NB_TRY(launch_predict(d, d.t_cur, 0, c->cfg.tick_exp, false, true, false, c->st));
+  NB_TRY(launch_actoff_identity(d, c->st));
+  NB_TRY(enqueue_force(c, nullptr, nullptr, 0, nullptr, 0, an + 3, 4, true, 0, 0, true, d.N));
+  const int64_t lo = cluster < 0 ? 0 : c->off_host[cluster];
+  const int64_t hi = cluster < 0 ? d.N : c->off_host[cluster + 1];
+  double* out = d.esum + 2 * kEnergyBlocks;
+  NB_TRY(launch_energy(d, an + 3, 4, lo, hi, d.esum, kEnergyBlocks, out, c->st));
+  double h[2];
+  NB_TRY(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, c->st));
+  const int rc = sync_status(c);
+  if (rc != NB_OK) return rc;
+  *ekin = h[0];
+  *epot = h[1];
+  return NB_OK;
+}
+
+int nb_get_state(nb_ctx* c, double* pos, double* vel, double* acc, double* jerk, int64_t* t,
+                 int32_t* level) {
+  if (!c) return NB_EINVAL;
+  const int64_t N = c->d.N;
+  // pack (n, 3) rows into the step scratch (acc_new / jerk_new), then copy
+  // straight into the caller's arrays
+  double* sa = reinterpret_cast<double*>(c->d.acc_new);
+  double* sb = reinterpret_cast<double*>(c->d.jerk_new);
+  const dbl4* srcs[4] = {c->d.pos, c->d.vel, c->d.acc, c->d.jerk};
+  double* dsts[4] = {pos, vel, acc, jerk};
+  for (int q = 0; q < 4; q += 2) {
+    for (int r = 0; r < 2; ++r) {
+      if (!dsts[q + r]) continue;
+      double* stage = r == 0 ? sa : sb;
+      NB_TRY(launch_unpack3(srcs[q + r], stage, N, c->st));
+      NB_TRY(cudaMemcpyAsync(dsts[q + r], stage, 24 * N, cudaMemcpyDeviceToHost, c->st));
+    }
+    NB_TRY(cudaStreamSynchronize(c->st));  // stage reuse by the next pair
+  }
+  if (t) NB_TRY(cudaMemcpyAsync(t, c->d.t, 8 * N, cudaMemcpyDeviceToHost, c->st));
+  if (level) NB_TRY(cudaMemcpyAsync(level, c->d.level, 4 * N, cudaMemcpyDeviceToHost, c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));
+  return NB_OK;
+}
+
+int nb_set_state(nb_ctx* c, const double* pos, const double* vel, const double* acc,
+                 const double* jerk, const int64_t* t, const int32_t* level) {
+  if (!c || !pos || !vel || !acc || !jerk || !t || !level) return NB_EINVAL;
+  const int64_t N = c->d.N;
+  const int T = c->cfg.tick_exp;
+  for (int64_t i = 0; i < N; ++i) {
+    if (level[i] < c->cfg.level_min || level[i] > c->cfg.level_max || t[i] < 0) return NB_EINVAL;
+    if (t[i] & (((int64_t)1 << (T - level[i])) - 1)) return NB_EINVAL;
+  }
+  if (!finite_all(pos, 3 * N) || !finite_all(vel, 3 * N) || !finite_all(acc, 3 * N) ||
+      !finite_all(jerk, 3 * N))
+    return NB_EINVAL;
+  double* sa = reinterpret_cast<double*>(c->d.acc_new);
+  double* sb = reinterpret_cast<double*>(c->d.jerk_new);
+  NB_TRY(cudaMemcpyAsync(sa, pos, 24 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(cudaMemcpyAsync(sb, vel, 24 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(launch_pack3(sa, c->d.pos, N, true, c->st));    // keeps the masses
+  NB_TRY(launch_pack3(sb, c->d.vel, N, false, c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));  // host arrays may be pageable: stage reuse
+  NB_TRY(cudaMemcpyAsync(sa, acc, 24 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(cudaMemcpyAsync(sb, jerk, 24 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(launch_pack3(sa, c->d.acc, N, true, c->st));    // keeps the potentials
+  NB_TRY(launch_pack3(sb, c->d.jerk, N, false, c->st));
+  NB_TRY(cudaMemcpyAsync(c->d.t, t, 8 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(cudaMemcpyAsync(c->d.level, level, 4 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(cudaMemsetAsync(c->d.t_cur, 0, 8 * (size_t)c->d.K, c->st));
+  NB_TRY(launch_tcur_from_t(c->d, c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));
+  return NB_OK;
+}
+
+int nb_stats(nb_ctx* c, int64_t* block_steps, int64_t* interactions, int64_t* t_min,
+             int64_t* t_max) {
+  if (!c) return NB_EINVAL;
+  unsigned long long ctr[4];
+  std::vector<int64_t> tc(c->d.K);
+  NB_TRY(cudaMemcpyAsync(ctr, c->d.counters, sizeof ctr, cudaMemcpyDeviceToHost, c->st));
+  NB_TRY(cudaMemcpyAsync(tc.data(), c->d.t_cur, 8 * c->d.K, cudaMemcpyDeviceToHost, c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));
+  if (block_steps) *block_steps = (int64_t)ctr[1];
+  if (interactions) *interactions = (int64_t)ctr[0];
+  int64_t lo = LLONG_MAX, hi = LLONG_MIN;
+  for (int64_t v : tc) {
+    lo = v < lo ? v : lo;
+    hi = v > hi ? v : hi;
+  }
+  if (t_min) *t_min = lo;
+  if (t_max) *t_max = hi;
+  return NB_OK;
+}
+
+int nb_profile_enable(nb_ctx* c, int enable) {
+  if (!c) return NB_EINVAL;
+  c->prof = enable != 0;
+  return NB_OK;
+}
+
+int nb_profile_read(nb_ctx* c, double* force_ms, int64_t* launches) {
+  if (!c) return NB_EINVAL;
+  NB_TRY(prof_collect(c, true));
+  if (force_ms) *force_ms = c->prof_ms;
+  if (launches) *launches = c->prof_launches;
+  c->prof_ms = 0.0;
+  c->prof_launches = 0;
+  return NB_OK;
+}
+
+int nb_status(nb_ctx* c) {
+  if (!c) return NB_EINVAL;
+  return sync_status(c);
+}
+
+int nb_clear_status(nb_ctx* c) {
+  if (!c) return NB_EINVAL;
+  NB_TRY(cudaMemsetAsync(c->d.status, 0, 4, c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));
+  return NB_OK;
+}
+
+const char* nb_strerror(int code) {
+  switch (code) {
+    case NB_OK: return "ok";
+    case NB_EINVAL: return "invalid argument";
+    case NB_ENOMEM: return "workspace too small";
+    case NB_ECUDA: return "CUDA runtime error";
+    case NB_ETIMEOUT: return "device wait timed out";
+    case NB_ENONFINITE: return "non-finite value produced";
+    case NB_ESTATE: return "invalid context state";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

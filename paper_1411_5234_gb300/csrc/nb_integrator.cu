@@ -1,0 +1,600 @@
+// nb_integrator.cu -- block-time-step machinery around the force kernels.
+//
+// One block step (Sec. 2 items 1 and 2) is a fixed sequence of launches whose
+// sizes all live on the device, so it can be captured in a CUDA graph:
+//   k_tmin     t_next(k) = min_i (t_i + dt_i) per cluster          (O(N))
+//   k_predict  Taylor predictor of EVERY particle to t_next, written
+//              as the source arrays; counts due particles per block (O(N))
+//   k_scan     exclusive scan of the per-block counts (one CTA)
+//   k_scatter  active list {i : t_i + dt_i = t_next}, ascending (O(N))
+//   k_plan     per-cluster i-split factor B_k and work-item offsets
+//   force      (nb_force_mixed.cu / nb_force_fp64.cu)          O(m N)
+//   k_reduce   fixed-order sum of the B_k partials per target
+//   k_correct  Hermite corrector, step criterion, power-of-two level (O(m))
+#include <cfloat>
+#include <climits>
+
+#include <math_constants.h>
+
+#include "nb_integrator.cuh"
+
+namespace nb {
+namespace {
+
+__device__ __forceinline__ int64_t step_ticks(int32_t level, int T) {
+  return (int64_t)1 << (T - level);
+}
+
+// Taylor predictor of the Hermite scheme: x + v t + a t^2/2 + j t^3/6 and
+// v + a t + j t^2/2 (Horner form).
+__device__ __forceinline__ void predict1(const dbl4& p, const dbl4& v, const dbl4& a,
+                                         const dbl4& j, double t, double3& xp, double3& vp) {
+  const double h = 0.5 * t, s = t * (1.0 / 3.0);
+  xp.x = p.x + t * (v.x + h * (a.x + s * j.x));
+  xp.y = p.y + t * (v.y + h * (a.y + s * j.y));
+  xp.z = p.z + t * (v.z + h * (a.z + s * j.z));
+  vp.x = v.x + t * (a.x + h * j.x);
+  vp.y = v.y + t * (a.y + h * j.y);
+  vp.z = v.z + t * (a.z + h * j.z);
+}
+
+__device__ __forceinline__ float hi_part(double x) { return __double2float_rn(x); }
+
+// Mixed source slot: component c of slot s lives at float index
+// ((s >> 2) * 10 + c) * 4 + (s & 3).
+__device__ __forceinline__ void write_mixed(float4* src, int64_t slot, const double3& x,
+                                            double m, const double3& v) {
+  float* g = reinterpret_cast<float*>(src + (slot >> 2) * 10) + (slot & 3);
+  const float xh = hi_part(x.x), yh = hi_part(x.y), zh = hi_part(x.z);
+  g[0] = xh;
+  g[4] = yh;
+  g[8] = zh;
+  g[12] = static_cast<float>(m);
+  g[16] = __double2float_rn(x.x - (double)xh);
+  g[20] = __double2float_rn(x.y - (double)yh);
+  g[24] = __double2float_rn(x.z - (double)zh);
+  g[28] = __double2float_rn(v.x);
+  g[32] = __double2float_rn(v.y);
+  g[36] = __double2float_rn(v.z);
+}
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T v, Op op, T* sh, T ident) {
+  // blockDim.x a multiple of 32, <= 1024
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (wid == 0) {
+    v = lane < nw ? sh[lane] : ident;
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (lane == 0) sh[0] = v;
+  }
+  __syncthreads();
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// inclusive warp scan
+__device__ __forceinline__ int32_t warp_incl_scan(int32_t v) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// exclusive block scan (blockDim.x <= 1024); returns the block total in *total
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int32_t inc = warp_incl_scan(v);
+  if (lane == 31) sh[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    int32_t x = lane < nw ? sh[lane] : 0;
+    x = warp_incl_scan(x);
+    sh[lane] = x;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int32_t base = wid > 0 ? sh[wid - 1] : 0;
+  *total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + inc - v;
+}
+
+// ----------------------------------------------------------------- kernels
+
+__global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// Massless pad sources (slots N_k .. round_up(N_k, 4) of each cluster), placed
+// far away so that every term they contribute is exactly zero.
+__global__ void k_init_pads(Dev d) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < d.K; k += gridDim.x * blockDim.x) {
+    const int64_t nk = d.off[k + 1] - d.off[k];
+    for (int64_t s = d.soff[k] + nk; s < d.soff[k + 1]; ++s) {
+      const double3 x = make_double3(kDummyPos, kDummyPos, kDummyPos);
+      const double3 v = make_double3(0.0, 0.0, 0.0);
+      write_mixed(d.src_mix, s, x, 0.0, v);
+      d.src64_pos[s] = dbl4{kDummyPos, kDummyPos, kDummyPos, 0.0};
+      d.src64_vel[s] = dbl4{0.0, 0.0, 0.0, 0.0};
+    }
+  }
+}
+
+// Next block time of every cluster whose time is below the end time.
+__global__ void k_tmin(Dev d, int T) {
+  __shared__ long long sh[32];
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x;
+  const int64_t i = i0 + threadIdx.x;
+  const int64_t t_end = *d.t_end;
+  int64_t due = LLONG_MAX;
+  int32_t c = -1;
+  if (i < d.N) {
+    c = d.cid[i];
+    if (d.t_cur[c] < t_end) due = d.t[i] + step_ticks(d.level[i], T);
+  }
+  // whole block inside one cluster: block min + one atomic
+  const int64_t ilast = min(i0 + (int64_t)blockDim.x, d.N) - 1;
+  const int32_t c0 = d.cid[i0], c1 = d.cid[ilast];
+  if (c0 == c1) {
+    const long long mn = block_reduce<long long>(
+        (long long)due, [](long long x, long long y) { return x < y ? x : y; }, sh, LLONG_MAX);
+    if (threadIdx.x == 0 && mn != LLONG_MAX)
+      atomicMin(reinterpret_cast<long long*>(d.t_min + c0), mn);
+  } else if (due != LLONG_MAX) {
+    atomicMin(reinterpret_cast<long long*>(d.t_min + c), (long long)due);
+  }
+}
+
+// Predict every particle to the target time of its cluster (t_tgt[c], or
+// t_fixed when t_tgt is null; clusters whose target is LLONG_MAX are left
+// alone) and write the source arrays.  With count_due, also count the
+// particles due at the target time per block of kScanBlock particles.
+__global__ void k_predict(Dev d, const int64_t* t_tgt, int64_t t_fixed, int T, int write_mix,
+                          int write64, int count_due) {
+  __shared__ int32_t sh[32];
+  const int64_t base = blockIdx.x * (int64_t)kScanBlock;
+  int32_t cnt = 0;
+#pragma unroll
+  for (int q = 0; q < kScanBlock / kScanThreads; ++q) {
+    const int64_t i = base + q * kScanThreads + threadIdx.x;
+    if (i >= d.N) break;
+    const int32_t c = d.cid[i];
+    const int64_t tn = t_tgt ? t_tgt[c] : t_fixed;
+    if (tn == LLONG_MAX) continue;
+    const int64_t ti = d.t[i];
+    if (count_due && ti + step_ticks(d.level[i], T) == tn) ++cnt;
+    const double tau = ldexp((double)(tn - ti), -T);
+    const dbl4 p = d.pos[i], v = d.vel[i], a = d.acc[i], j = d.jerk[i];
+    double3 xp, vp;
+    predict1(p, v, a, j, tau, xp, vp);
+    const int64_t slot = d.soff[c] + (i - d.off[c]);
+    if (write_mix) write_mixed(d.src_mix, slot, xp, p.w, vp);
+    if (write64) {
+      d.src64_pos[slot] = dbl4{xp.x, xp.y, xp.z, p.w};
+      d.src64_vel[slot] = dbl4{vp.x, vp.y, vp.z, 0.0};
+    }
+  }
+  if (count_due) {
+    const int32_t tot =
+        block_reduce<int32_t>(cnt, [](int32_t x, int32_t y) { return x + y; }, sh, 0);
+    if (threadIdx.x == 0) d.blk_count[blockIdx.x] = tot;
+  }
+}
+
+// Exclusive scan of nblk block counts (one CTA of 1024 threads); the total
+// goes to act_off[K].
+__global__ void k_scan(Dev d, int32_t nblk) {
+  __shared__ int32_t sh[32];
+  int32_t carry = 0;
+  for (int32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
+    const int32_t b = b0 + threadIdx.x;
+    const int32_t v = b < nblk ? d.blk_count[b] : 0;
+    int32_t tot;
+    const int32_t ex = block_excl_scan(v, sh, &tot);
+    if (b < nblk) d.blk_count[b] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) d.act_off[d.K] = carry;
+}
+
+// Active list in ascending particle order, plus each cluster's offset in it.
+__global__ void k_scatter(Dev d, int T) {
+  __shared__ int32_t sh[32];
+  const int64_t base = blockIdx.x * (int64_t)kScanBlock;
+  int32_t run = d.blk_count[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanBlock / kScanThreads; ++q) {
+    const int64_t i = base + q * kScanThreads + threadIdx.x;
+    int32_t f = 0, c = -1;
+    if (i < d.N) {
+      c = d.cid[i];
+      const int64_t tn = d.t_min[c];
+      f = (tn != LLONG_MAX && d.t[i] + step_ticks(d.level[i], T) == tn) ? 1 : 0;
+    }
+    int32_t tot;
+    const int32_t ex = block_excl_scan(f, sh, &tot);
+    if (i < d.N) {
+      if (f) d.active[run + ex] = static_cast<int32_t>(i);
+      if (i == d.off[c]) d.act_off[c] = run + ex;
+    }
+    run += tot;
+  }
+}
+
+// Work plan: per-cluster active count m_k, i-split factor B_k (Sec. 2 item 3)
+// and work-item offsets.  One CTA.
+__global__ void k_plan(Dev d, PlanArgs p) {
+  __shared__ unsigned long long shu[32];
+  __shared__ int32_t shi[32];
+  __shared__ int32_t bg_sh;
+  const int32_t K = d.K;
+  unsigned long long nit = 0, inter = 0;
+  for (int32_t k = threadIdx.x; k < K; k += blockDim.x) {
+    const int64_t mk = d.act_off[k + 1] - d.act_off[k];
+    nit += (unsigned long long)ceil_div64(mk, p.NI);
+    inter += (unsigned long long)mk * (unsigned long long)(d.off[k + 1] - d.off[k]);
+  }
+  auto add = [](unsigned long long x, unsigned long long y) { return x + y; };
+  nit = block_reduce<unsigned long long>(nit, add, shu, 0ull);
+  inter = block_reduce<unsigned long long>(inter, add, shu, 0ull);
+  if (threadIdx.x == 0) {
+    int64_t bg = 1;
+    if (nit > 0) {
+      if (p.forced_b > 0) {
+        bg = p.forced_b;
+      } else {
+        // fill the persistent grid, then pick the split whose last round of
+        // work items is fullest
+        const int64_t b0 = max((int64_t)1, ceil_div64(p.grid, (int64_t)nit));
+        double best = -1.0;
+        for (int64_t b = b0; b <= 2 * b0 + 2; ++b) {
+          const int64_t items = (int64_t)nit * b;
+          const double eff = (double)items / (double)(ceil_div64(items, p.grid) * p.grid);
+          if (eff > best + 1e-3) { best = eff; bg = b; }
+        }
+      }
+      const int64_t cap = max((int64_t)1, p.part_items / (int64_t)nit);
+      if (bg > cap) bg = cap;
+    }
+    bg_sh = static_cast<int32_t>(bg);
+    if (p.count) {
+      atomicAdd(d.counters + 0, inter);
+      if (p.step_mode) atomicAdd(d.counters + 1, 1ull);
+    }
+  }
+  __syncthreads();
+  const int32_t bg = bg_sh;
+  int32_t carry = 0;
+  for (int32_t k0 = 0; k0 < K; k0 += blockDim.x) {
+    const int32_t k = k0 + threadIdx.x;
+    int32_t items = 0;
+    if (k < K) {
+      const int64_t mk = d.act_off[k + 1] - d.act_off[k];
+      const int64_t Sk = d.soff[k + 1] - d.soff[k];
+      int64_t B = min((int64_t)bg, ceil_div64(Sk, p.JT));
+      if (B < 1) B = 1;
+      B = ceil_div64(Sk, chunk_len(Sk, B, p.JT));  // every chunk non-empty
+      d.bfac[k] = static_cast<int32_t>(B);
+      items = static_cast<int32_t>(ceil_div64(mk, p.NI) * B);
+      if (p.step_mode) {
+        const int64_t tn = d.t_min[k];
+        if (tn != LLONG_MAX) d.t_cur[k] = tn;
+        d.t_min[k] = LLONG_MAX;
+      }
+    }
+    int32_t tot;
+    const int32_t ex = block_excl_scan(items, shi, &tot);
+    if (k < K) d.item_off[k] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) d.item_off[K] = carry;
+}
+
+// Fixed-order sum of the B_k partials of every target whose cluster was split.
+__global__ void k_reduce(ForceArgs a, int NI, int with_acc) {
+  const int32_t m = a.act_off[a.K];
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {
+    const int32_t k = upper_bound_i32(a.act_off, a.K + 1, s) - 1;
+    const int32_t B = a.bfac[k];
+    if (B <= 1) continue;
+    const int32_t local = s - a.act_off[k];
+    const int32_t it = local / NI, q = local - it * NI;
+    const int32_t w0 = a.item_off[k] + it * B;
+    double v[kPartialComps];
+#pragma unroll
+    for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
+    for (int32_t b = 0; b < B; ++b) {
+      const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
+#pragma unroll
+      for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
+    }
+    if (with_acc) {
+      if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[(int64_t)s * a.sa + c] = a.G * v[c];
+      if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[(int64_t)s * a.sj + c] = a.G * v[3 + c];
+    }
+    if (a.out_pot) a.out_pot[(int64_t)s * a.sp] = a.G * v[6];
+  }
+}
+
+__device__ __forceinline__ double norm3(double x, double y, double z) {
+  return sqrt(x * x + y * y + z * z);
+}
+
+// Step criterion of Aarseth (the paper's reference for its block steps):
+// dt = sqrt(eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)); +inf when the
+// denominator vanishes.
+__device__ __forceinline__ double aarseth(double na, double nj, double n2, double n3, double eta) {
+  const double den = nj * n3 + n2 * n2;
+  if (!(den > 0.0)) return CUDART_INF;
+  return sqrt(eta * (na * n2 + nj * nj) / den);
+}
+
+// Power-of-two level: the largest 2^-L not above dt (via frexp), clamped to
+// [lmin, lmax]; growth by one level at most and only when the new time is a
+// multiple of the doubled step; L_old < 0 means no previous level.
+__device__ __forceinline__ int32_t new_level(double dt, int32_t L_old, int64_t t_new, int T,
+                                             int lmin, int lmax) {
+  int L;
+  if (!(dt > 0.0)) {
+    L = lmax;
+  } else if (isinf(dt)) {
+    L = lmin;
+  } else {
+    int e;
+    (void)frexp(dt, &e);
+    L = 1 - e;
+  }
+  L = min(max(L, lmin), lmax);
+  if (L_old < 0 || L >= L_old) return L;
+  const int Ld = L_old - 1;
+  if (Ld < lmin) return L_old;
+  return (t_new % ((int64_t)1 << (T - Ld)) == 0) ? Ld : L_old;
+}
+
+// Hermite corrector (Sec. 2 item 1) of the listed particles, new step level,
+// and the state write-back.
+__global__ void k_correct(Dev d, CorrectArgs c) {
+  const int64_t m = c.count_dev ? (int64_t)*c.count_dev : c.count_host;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < m;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = c.active[s];
+    if (i < 0 || i >= d.N) {
+      atomicOr(d.status, kStatusInval);
+      continue;
+    }
+    const int32_t cl = d.cid[i];
+    const int64_t tn = c.t_tgt ? c.t_tgt[cl] : c.t_fixed;
+    const int64_t ti = d.t[i];
+    if (tn <= ti) {  // a step must move forward in time
+      atomicOr(d.status, kStatusInval);
+      continue;
+    }
+    const double t = ldexp((double)(tn - ti), -c.T);
+    const dbl4 p = d.pos[i], v = d.vel[i], a0 = d.acc[i], j0 = d.jerk[i];
+    double3 xp, vp;
+    predict1(p, v, a0, j0, t, xp, vp);
+    const double a1[3] = {c.acc[s * c.sa], c.acc[s * c.sa + 1], c.acc[s * c.sa + 2]};
+    const double j1[3] = {c.jerk[s * c.sj], c.jerk[s * c.sj + 1], c.jerk[s * c.sj + 2]};
+    const double a0v[3] = {a0.x, a0.y, a0.z}, j0v[3] = {j0.x, j0.y, j0.z};
+    const double xpv[3] = {xp.x, xp.y, xp.z}, vpv[3] = {vp.x, vp.y, vp.z};
+    const double t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
+    double x1[3], v1[3], a2e[3], a3[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double da = a0v[q] - a1[q];
+      const double a2 = (-6.0 * da - t * (4.0 * j0v[q] + 2.0 * j1[q])) / t2;
+      a3[q] = (12.0 * da + 6.0 * t * (j0v[q] + j1[q])) / t3;
+      x1[q] = xpv[q] + a2 * t4 / 24.0 + a3[q] * t5 / 120.0;
+      v1[q] = vpv[q] + a2 * t3 / 6.0 + a3[q] * t4 / 24.0;
+      a2e[q] = a2 + a3[q] * t;
+    }
+    const double dt = aarseth(norm3(a1[0], a1[1], a1[2]), norm3(j1[0], j1[1], j1[2]),
+                              norm3(a2e[0], a2e[1], a2e[2]), norm3(a3[0], a3[1], a3[2]), c.eta);
+    const int32_t L = new_level(dt, d.level[i], tn, c.T, c.lmin, c.lmax);
+    bool finite = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) finite = finite && isfinite(x1[q]) && isfinite(v1[q]);
+    if (!finite) atomicOr(d.status, kStatusNonFinite);
+    const double pot = c.pot ? c.pot[s * c.sp] : a0.w;
+    d.pos[i] = dbl4{x1[0], x1[1], x1[2], p.w};
+    d.vel[i] = dbl4{v1[0], v1[1], v1[2], 0.0};
+    d.acc[i] = dbl4{a1[0], a1[1], a1[2], pot};
+    d.jerk[i] = dbl4{j1[0], j1[1], j1[2], 0.0};
+    d.t[i] = tn;
+    d.level[i] = L;
+  }
+}
+
+// Initial state: a0, jerk0 from the t = 0 force (identity active list) and
+// the first level from eta_start |a| / |jerk|.
+__global__ void k_init_levels(Dev d, double eta_s, int T, int lmin, int lmax) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const dbl4 a = d.acc_new[i], j = d.jerk_new[i];
+    d.acc[i] = a;
+    d.jerk[i] = dbl4{j.x, j.y, j.z, 0.0};
+    const double nj = norm3(j.x, j.y, j.z);
+    const double dt = nj > 0.0 ? eta_s * norm3(a.x, a.y, a.z) / nj : CUDART_INF;
+    d.level[i] = new_level(dt, -1, 0, T, lmin, lmax);
+    d.t[i] = 0;
+  }
+}
+
+// Cluster offsets of a caller's active list (lower bounds of the cluster
+// starts) and its validation: strictly ascending, inside [0, N).
+__global__ void k_actoff_list(Dev d, const int32_t* list, int64_t m) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = tid; s < m; s += nth) {
+    const int32_t v = list[s];
+    if (v < 0 || v >= d.N || (s + 1 < m && list[s + 1] <= v)) atomicOr(d.status, kStatusInval);
+  }
+  for (int64_t k = tid; k <= d.K; k += nth) {
+    const int64_t key = d.off[k];
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)list[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    d.act_off[k] = static_cast<int32_t>(k == d.K ? m : lo);
+  }
+}
+
+// Identity active list: every particle of every cluster is a target.
+__global__ void k_actoff_identity(Dev d) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= d.K;
+       k += (int64_t)gridDim.x * blockDim.x)
+    d.act_off[k] = static_cast<int32_t>(d.off[k]);
+}
+
+// Energy: per-block partial sums (fixed ranges) of 1/2 m v^2 from the FP64
+// predicted velocities and of 1/2 m pot; then one CTA sums the partials in
+// block order (deterministic).
+__global__ void k_energy_partial(Dev d, const double* pot, int sp, int64_t lo, int64_t hi,
+                                 double* out) {
+  __shared__ double sh[32];
+  double ek = 0.0, ep = 0.0;
+  for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = d.cid[i];
+    const int64_t slot = d.soff[c] + (i - d.off[c]);
+    const dbl4 v = d.src64_vel[slot];
+    const double m = d.pos[i].w;
+    ek += 0.5 * m * (v.x * v.x + v.y * v.y + v.z * v.z);
+    ep += 0.5 * m * pot[i * sp];
+  }
+  auto add = [](double x, double y) { return x + y; };
+  ek = block_reduce<double>(ek, add, sh, 0.0);
+  ep = block_reduce<double>(ep, add, sh, 0.0);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = ek;
+    out[2 * blockIdx.x + 1] = ep;
+  }
+}
+
+__global__ void k_energy_final(double* part, int nblk, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double hk = 0.0, lk = 0.0, hp = 0.0, lp = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      two_sum_acc(hk, lk, part[2 * b]);
+      two_sum_acc(hp, lp, part[2 * b + 1]);
+    }
+    out[0] = hk + lk;
+    out[1] = hp + lp;
+  }
+}
+
+// (n, 3) rows <-> double4 rows; keep_w keeps the destination's 4th lane
+// (mass in pos, potential in acc), otherwise it is zeroed.
+__global__ void k_pack3(const double* src3, dbl4* dst, int64_t n, int keep_w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = keep_w ? dst[i].w : 0.0;
+    dst[i] = dbl4{src3[3 * i], src3[3 * i + 1], src3[3 * i + 2], w};
+  }
+}
+
+__global__ void k_unpack3(const dbl4* src, double* dst3, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const dbl4 v = src[i];
+    dst3[3 * i] = v.x;
+    dst3[3 * i + 1] = v.y;
+    dst3[3 * i + 2] = v.z;
+  }
+}
+
+// Current block time of each cluster = the latest particle time in it.
+__global__ void k_tcur_from_t(Dev d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicMax(reinterpret_cast<long long*>(d.t_cur + d.cid[i]), (long long)d.t[i]);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------- launchers
+static inline int blocks_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t b = ceil_div64(n > 0 ? n : 1, threads);
+  return static_cast<int>(b < cap ? b : cap);
+}
+
+cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t st) {
+  k_fill_i64<<<blocks_for(n, 256), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_pads(const Dev& d, cudaStream_t st) {
+  k_init_pads<<<blocks_for(d.K, 128), 128, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st) {
+  k_tmin<<<static_cast<int>(ceil_div64(d.N, 256)), 256, 0, st>>>(d, T);
+  return cudaGetLastError();
+}
+int scan_blocks(int64_t N) { return static_cast<int>(ceil_div64(N, kScanBlock)); }
+cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T,
+                           bool mix, bool f64, bool count_due, cudaStream_t st) {
+  k_predict<<<scan_blocks(d.N), kScanThreads, 0, st>>>(d, t_tgt, t_fixed, T, mix, f64, count_due);
+  return cudaGetLastError();
+}
+cudaError_t launch_compact(const Dev& d, int T, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(d, scan_blocks(d.N));
+  k_scatter<<<scan_blocks(d.N), kScanThreads, 0, st>>>(d, T);
+  return cudaGetLastError();
+}
+cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
+  k_plan<<<1, 512, 0, st>>>(d, p);
+  return cudaGetLastError();
+}
+cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
+                          cudaStream_t st) {
+  k_reduce<<<blocks_for(m_bound, 256), 256, 0, st>>>(a, NI, with_acc ? 1 : 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {
+  k_correct<<<blocks_for(m_bound, 128), 128, 0, st>>>(d, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,
+                               cudaStream_t st) {
+  k_init_levels<<<blocks_for(d.N, 256), 256, 0, st>>>(d, eta_s, T, lmin, lmax);
+  return cudaGetLastError();
+}
+cudaError_t launch_actoff_list(const Dev& d, const int32_t* list, int64_t m, cudaStream_t st) {
+  k_actoff_list<<<blocks_for(m > d.K ? m : d.K + 1, 256), 256, 0, st>>>(d, list, m);
+  return cudaGetLastError();
+}
+cudaError_t launch_actoff_identity(const Dev& d, cudaStream_t st) {
+  k_actoff_identity<<<blocks_for(d.K + 1, 256), 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_energy(const Dev& d, const double* pot, int sp, int64_t lo, int64_t hi,
+                          double* part, int nblk, double* out, cudaStream_t st) {
+  k_energy_partial<<<nblk, 256, 0, st>>>(d, pot, sp, lo, hi, part);
+  k_energy_final<<<1, 32, 0, st>>>(part, nblk, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack3(const double* src3, dbl4* dst, int64_t n, bool keep_w, cudaStream_t st) {
+  k_pack3<<<blocks_for(n, 256), 256, 0, st>>>(src3, dst, n, keep_w ? 1 : 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack3(const dbl4* src, double* dst3, int64_t n, cudaStream_t st) {
+  k_unpack3<<<blocks_for(n, 256), 256, 0, st>>>(src, dst3, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_tcur_from_t(const Dev& d, cudaStream_t st) {
+  k_tcur_from_t<<<blocks_for(d.N, 256), 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace nb

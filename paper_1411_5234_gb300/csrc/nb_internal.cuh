@@ -1,0 +1,228 @@
+// nb_internal.cuh -- internal types and device helpers of libnbody_gb300.
+//
+// Data layout in HBM (one caller-owned workspace, carved by nb_layout()):
+//   per particle i (N):   pos dbl4 (x, y, z, m)      vel dbl4 (vx, vy, vz, 0)
+//                         acc dbl4 (ax, ay, az, pot) jerk dbl4 (jx, jy, jz, 0)
+//                         t int64 ticks, level int32, cluster id int32,
+//                         active list int32, new acc/jerk dbl4 per active slot
+//   per source slot (S = sum over clusters of N_k rounded up to 4; pad slots
+//   hold massless dummies far away):
+//     mixed sources: groups of 4 slots, 10 float4 per group, component-major
+//       [xh][yh][zh][m][xl][yl][zl][vx][vy][vz], x = xh + xl (double-single),
+//       so one 16-byte shared-memory load yields a component of 4 sources and
+//       two f32x2 operand pairs;
+//     FP64 sources: dbl4 (x, y, z, m) and dbl4 (vx, vy, vz, 0).
+//   per cluster k (K):    particle / slot offsets, current block time,
+//                         running min for the next block time, active-list
+//                         offsets, i-split factor B_k, work-item offsets.
+//   i-split partial sums: [item][7][NI] doubles (acc xyz, jerk xyz, pot).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+// 32-byte aligned double vector (CUDA 13 names the alignment explicitly).
+typedef double4_32a dbl4;
+
+namespace nb {
+
+constexpr int kMaxTickExp = 60;
+constexpr int kScanBlock = 1024;     // particles per block in predict/scatter
+constexpr int kScanThreads = 256;
+constexpr int kPartialComps = 7;     // ax ay az jx jy jz pot
+constexpr double kDummyPos = 1.0e18; // where massless pad sources sit
+
+// Mixed-precision force kernel shape.
+constexpr int kMixNT = 128;          // threads per CTA
+constexpr int kMixIPT = 2;           // targets (i) per thread
+constexpr int kMixNI = kMixNT * kMixIPT;
+constexpr int kMixJT = 128;          // sources per shared-memory tile (multiple of 4)
+// FP64 force kernel shape.
+constexpr int kF64NT = 128;
+constexpr int kF64NI = kF64NT;
+constexpr int kF64JT = 64;
+
+// Device status bits (sticky; the host maps the lowest set code).
+constexpr uint32_t kStatusInval = 1u << 0;
+constexpr uint32_t kStatusTimeout = 1u << 1;
+constexpr uint32_t kStatusNonFinite = 1u << 2;
+
+struct Dev {
+  int64_t N = 0, S = 0;
+  int32_t K = 0;
+  dbl4 *pos = nullptr, *vel = nullptr, *acc = nullptr, *jerk = nullptr;
+  int64_t* t = nullptr;
+  int32_t* level = nullptr;
+  int32_t* cid = nullptr;
+  int32_t* active = nullptr;
+  dbl4 *acc_new = nullptr, *jerk_new = nullptr;
+  float4* src_mix = nullptr;     // (S / 4) * 10 float4
+  dbl4* src64_pos = nullptr;  // S
+  dbl4* src64_vel = nullptr;  // S
+  double* partials = nullptr;    // part_items * 7 * NI_max
+  int64_t part_items = 0;
+  int32_t* blk_count = nullptr;  // ceil(N / kScanBlock) + 1
+  int64_t *off = nullptr, *soff = nullptr;   // K + 1
+  int64_t *t_cur = nullptr, *t_min = nullptr; // K
+  int32_t *act_off = nullptr, *item_off = nullptr; // K + 1
+  int32_t* bfac = nullptr;       // K
+  double* esum = nullptr;        // energy partial sums
+  uint32_t* status = nullptr;
+  unsigned long long* counters = nullptr;  // [0] interactions [1] block steps
+  int64_t* t_end = nullptr;      // 1
+};
+
+// Targets, sources and outputs of one force launch.
+struct ForceArgs {
+  const int64_t* off;       // particle offsets of the clusters (K + 1)
+  const int64_t* soff;      // source-slot offsets (K + 1)
+  const int32_t* active;    // target particle indices (nullptr: identity)
+  const int32_t* act_off;   // target offsets per cluster (K + 1)
+  const int32_t* item_off;  // work-item offsets per cluster (K + 1)
+  const int32_t* bfac;      // i-split factor per cluster (K)
+  int32_t K;
+  const void* src_a;        // mixed: float4 groups; FP64: positions
+  const void* src_b;        // FP64: velocities
+  double* out_acc; int sa;  // row stride in doubles (nullptr: not written)
+  double* out_jerk; int sj;
+  double* out_pot; int sp;
+  double* partials;         // [item][7][NI]
+  double G;
+  double eps2;
+  uint32_t* status;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One-dimensional bulk copy global -> shared (TMA engine); completion is
+// signalled on `bar` as transaction bytes.  dst, src and bytes must be
+// multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Spin on an mbarrier phase with a clock budget; false when the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > budget) return false;
+  }
+}
+
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
+
+// Packed FP32 pairs (f32x2): one instruction does the same operation on two
+// independent lanes held in a 64-bit register pair.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(f2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// Hardware approximate reciprocal square root / reciprocal (SFU, FP32).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Knuth's error-free two-sum: hi + lo accumulates x exactly up to the final
+// rounding of lo.
+template <typename T>
+__device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T x) {
+  T s = hi + x;
+  T bp = s - hi;
+  T err = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += err;
+}
+
+__device__ __forceinline__ int32_t upper_bound_i32(const int32_t* a, int32_t n, int32_t v) {
+  // first index k in [0, n) with a[k] > v (a ascending)
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) > v) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t round_up64(int64_t a, int64_t b) { return ceil_div64(a, b) * b; }
+
+// Chunk length (in source slots) of the j-range split of a cluster with S_k
+// slots into B chunks; a multiple of the tile length JT.  The plan shrinks B
+// so that every one of the B chunks is non-empty.
+__host__ __device__ __forceinline__ int64_t chunk_len(int64_t S_k, int64_t B, int64_t JT) {
+  return round_up64(ceil_div64(S_k, B), JT);
+}
+
+// ------------------------------------------------------- launch wrappers
+// (defined in the .cu files; all enqueue on `st` and return the launch error)
+cudaError_t launch_force_mixed(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st);
+cudaError_t launch_force_fp64(const ForceArgs& a, int grid, int mode, cudaStream_t st);
+int force_mixed_ctas_per_sm();
+int force_fp64_ctas_per_sm();
+size_t force_mixed_smem();
+size_t force_fp64_smem();
+
+enum { kF64Full = 0, kF64PotOnly = 1 };
+
+}  // namespace nb

@@ -1,0 +1,289 @@
+"""ctypes binding of libnbody_gb300.so (the C ABI in include/nbody_gb300.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  PyTorch supplies the device workspace (one uint8 tensor) and the
+stream.  Importing this module loads the library; a missing library raises
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ETIMEOUT, NB_ENONFINITE, NB_ESTATE = range(7)
+NB_FP64, NB_MIXED = 0, 1
+
+FUNCTIONS = [
+    "nb_default_config", "nb_workspace_size", "nb_init", "nb_free", "nb_predict", "nb_force",
+    "nb_correct", "nb_step_block", "nb_set_end_time", "nb_energy", "nb_get_state",
+    "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
+    "nb_profile_enable", "nb_profile_read",
+]
+
+
+class NbConfig(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("eps", ctypes.c_double), ("eta", ctypes.c_double),
+                ("eta_start", ctypes.c_double), ("level_min", ctypes.c_int32),
+                ("level_max", ctypes.c_int32), ("tick_exp", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("bfactor", ctypes.c_int32),
+                ("graph_steps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class NBError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+def library_path() -> str:
+    return os.environ.get("NBODY_GB300_LIB", _build.LIB)
+
+
+def _load() -> ctypes.CDLL:
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnbody_gb300.so not found at {path}; build it with "
+                           "`python -m paper_1411_5234_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "nb_default_config": (None, [P]),
+        "nb_workspace_size": (ctypes.c_int, [i64, i32, P, P]),
+        "nb_init": (ctypes.c_int, [P, P, i32, P, P, P, P, P, ctypes.c_size_t, P]),
+        "nb_free": (None, [P]),
+        "nb_predict": (ctypes.c_int, [P, i64]),
+        "nb_force": (ctypes.c_int, [P, P, i64, P, P, P]),
+        "nb_correct": (ctypes.c_int, [P, i64, P, i64, P, P]),
+        "nb_step_block": (ctypes.c_int, [P, i64]),
+        "nb_set_end_time": (ctypes.c_int, [P, i64]),
+        "nb_energy": (ctypes.c_int, [P, i32, P, P]),
+        "nb_get_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
+        "nb_set_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
+        "nb_stats": (ctypes.c_int, [P, P, P, P, P]),
+        "nb_status": (ctypes.c_int, [P]),
+        "nb_clear_status": (ctypes.c_int, [P]),
+        "nb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "nb_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "nb_profile_read": (ctypes.c_int, [P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def strerror(code: int) -> str:
+    return lib.nb_strerror(int(code)).decode()
+
+
+def _check(rc, where):
+    if rc != NB_OK:
+        raise NBError(rc, where)
+
+
+def default_config(**kw) -> NbConfig:
+    cfg = NbConfig()
+    lib.nb_default_config(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(f"nb_config has no field {k!r}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+def workspace_size(n_total: int, n_clusters: int, cfg: NbConfig) -> int:
+    out = ctypes.c_size_t()
+    _check(lib.nb_workspace_size(int(n_total), int(n_clusters), ctypes.byref(cfg),
+                                 ctypes.byref(out)), "nb_workspace_size")
+    return int(out.value)
+
+
+def _hptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Stats:
+    block_steps: int
+    interactions: int
+    t_min: int
+    t_max: int
+
+
+class Sim:
+    """A library context over caller-owned device memory.
+
+    ``offsets`` (n_clusters + 1) delimit independent clusters; ``mass`` (n),
+    ``pos``/``vel`` (n, 3) are host arrays in any float type.  The workspace
+    is one torch uint8 tensor on the current CUDA device; work runs on
+    ``stream`` (a dedicated torch stream by default, so that block-step
+    sequences can be captured in CUDA graphs).
+    """
+
+    def __init__(self, pos, vel, mass, offsets=None, cfg: NbConfig | None = None,
+                 stream: torch.cuda.Stream | None = None, **cfg_kw):
+        self.cfg = cfg if cfg is not None else default_config()
+        for k, v in cfg_kw.items():
+            setattr(self.cfg, k, v)
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        n = pos.shape[0]
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(n, 3)
+        mass = np.ascontiguousarray(mass, dtype=np.float64).reshape(n)
+        if offsets is None:
+            offsets = np.array([0, n], dtype=np.int64)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.n = n
+        self.n_clusters = int(offsets.shape[0] - 1)
+        self.offsets = offsets.copy()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.ws_bytes = workspace_size(n, self.n_clusters, self.cfg)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        self._ctx = ctypes.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        rc = lib.nb_init(ctypes.byref(self._ctx), ctypes.byref(self.cfg), self.n_clusters,
+                         _hptr(offsets), _hptr(mass), _hptr(pos), _hptr(vel),
+                         ctypes.c_void_p(self.workspace.data_ptr()), self.ws_bytes,
+                         ctypes.c_void_p(self.stream.cuda_stream))
+        _check(rc, "nb_init")
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib.nb_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- time ------------------------------------------------------------
+    def ticks(self, t: float) -> int:
+        return int(round(t * 2.0 ** self.cfg.tick_exp))
+
+    def time(self, ticks: int) -> float:
+        return float(np.ldexp(float(ticks), -self.cfg.tick_exp))
+
+    # -- hot path --------------------------------------------------------
+    def predict(self, t_ticks: int):
+        _check(lib.nb_predict(self._ctx, int(t_ticks)), "nb_predict")
+
+    def force(self, active: torch.Tensor, acc: torch.Tensor | None = None,
+              jerk: torch.Tensor | None = None, pot: torch.Tensor | None = None,
+              want_pot: bool = True):
+        """Forces on ``active`` (int32 CUDA tensor, ascending) from the last prediction."""
+        if active.dtype != torch.int32 or not active.is_cuda or not active.is_contiguous():
+            raise ValueError("active must be a contiguous int32 CUDA tensor")
+        m = active.numel()
+        if acc is None:
+            acc = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+        if jerk is None:
+            jerk = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+        if pot is None and want_pot:
+            pot = torch.empty(m, dtype=torch.float64, device="cuda")
+        self._order_inputs(active, acc, jerk, pot)
+        _check(lib.nb_force(self._ctx, _dptr(active), m, _dptr(acc), _dptr(jerk), _dptr(pot)),
+               "nb_force")
+        self._order_outputs(acc, jerk, pot)
+        return acc, jerk, pot
+
+    def correct(self, t_ticks: int, active: torch.Tensor, acc: torch.Tensor, jerk: torch.Tensor):
+        self._order_inputs(active, acc, jerk)
+        _check(lib.nb_correct(self._ctx, int(t_ticks), _dptr(active), active.numel(),
+                              _dptr(acc), _dptr(jerk)), "nb_correct")
+
+    def step(self, n_steps: int = 1):
+        _check(lib.nb_step_block(self._ctx, int(n_steps)), "nb_step_block")
+
+    def set_end_time(self, t_end_ticks: int):
+        _check(lib.nb_set_end_time(self._ctx, int(t_end_ticks)), "nb_set_end_time")
+
+    # -- host-synchronising calls -----------------------------------------
+    def energy(self, cluster: int = -1):
+        ek, ep = ctypes.c_double(), ctypes.c_double()
+        _check(lib.nb_energy(self._ctx, int(cluster), ctypes.byref(ek), ctypes.byref(ep)),
+               "nb_energy")
+        return ek.value, ep.value
+
+    def get_state(self):
+        n = self.n
+        pos, vel, acc, jerk = (np.empty((n, 3)) for _ in range(4))
+        t = np.empty(n, dtype=np.int64)
+        level = np.empty(n, dtype=np.int32)
+        _check(lib.nb_get_state(self._ctx, _hptr(pos), _hptr(vel), _hptr(acc), _hptr(jerk),
+                                _hptr(t), _hptr(level)), "nb_get_state")
+        return dict(pos=pos, vel=vel, acc=acc, jerk=jerk, t=t, level=level)
+
+    def set_state(self, pos, vel, acc, jerk, t, level):
+        n = self.n
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(n, 3) for a in (pos, vel, acc, jerk)]
+        t = np.ascontiguousarray(t, dtype=np.int64).reshape(n)
+        level = np.ascontiguousarray(level, dtype=np.int32).reshape(n)
+        _check(lib.nb_set_state(self._ctx, *[_hptr(a) for a in arrs], _hptr(t), _hptr(level)),
+               "nb_set_state")
+
+    def stats(self) -> Stats:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib.nb_stats(self._ctx, *[ctypes.byref(x) for x in v]), "nb_stats")
+        return Stats(*[x.value for x in v])
+
+    def profile(self, enable: bool = True):
+        """Bracket every force-kernel launch with CUDA events (no graphs meanwhile)."""
+        _check(lib.nb_profile_enable(self._ctx, int(bool(enable))), "nb_profile_enable")
+
+    def profile_read(self):
+        """(force-kernel milliseconds, launches) since the previous read."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib.nb_profile_read(self._ctx, ctypes.byref(ms), ctypes.byref(n)),
+               "nb_profile_read")
+        return ms.value, n.value
+
+    def get_state_into(self, pos, vel, acc, jerk, t, level):
+        """nb_get_state into caller-provided (e.g. pinned) numpy arrays."""
+        _check(lib.nb_get_state(self._ctx, *[None if a is None else _hptr(a)
+                                             for a in (pos, vel, acc, jerk, t, level)]),
+               "nb_get_state")
+
+    def status(self) -> int:
+        return int(lib.nb_status(self._ctx))
+
+    def clear_status(self):
+        _check(lib.nb_clear_status(self._ctx), "nb_clear_status")
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    # -- stream ordering between torch's current stream and the library's --
+    def _order_inputs(self, *tensors):
+        cur = torch.cuda.current_stream()
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        for t in tensors:
+            if t is not None:
+                t.record_stream(self.stream)
+
+    def _order_outputs(self, *tensors):
+        cur = torch.cuda.current_stream()
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)

@@ -1,0 +1,65 @@
+"""The C ABI: the library builds for sm_103a, loads without a GPU, and exports
+every entry point that include/nbody_gb300.h declares (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nbody_gb300.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nb_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1411_5234_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for required in ("nb_init", "nb_predict", "nb_force", "nb_correct", "nb_energy",
+                     "nb_step_block"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(libpath):
+    from paper_1411_5234_gb300 import nbody
+    assert sorted(nbody.FUNCTIONS) == declared_functions()
+
+
+def test_host_only_calls(libpath):
+    # calls that never touch the device: config, sizes, error strings
+    from paper_1411_5234_gb300 import nbody
+    cfg = nbody.default_config()
+    assert cfg.G == 1.0 and cfg.eta == 0.01 and cfg.precision == nbody.NB_MIXED
+    assert nbody.workspace_size(1024, 1, cfg) > 1024 * 128
+    assert nbody.workspace_size(2000, 7, cfg) >= nbody.workspace_size(1993, 1, cfg)
+    with pytest.raises(nbody.NBError):
+        nbody.workspace_size(0, 1, cfg)
+    bad = nbody.default_config(level_min=5, level_max=3)
+    with pytest.raises(nbody.NBError):
+        nbody.workspace_size(100, 1, bad)
+    assert nbody.strerror(nbody.NB_EINVAL) == "invalid argument"
+    assert nbody.strerror(99) == "unknown status"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    import subprocess
+    import sys
+    env = dict(os.environ, NBODY_GB300_LIB=str(tmp_path / "nope.so"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1411_5234_gb300.nbody"], cwd=ROOT,
+                       env=env, capture_output=True, text=True)
+    assert r.returncode != 0 and "not found" in r.stderr

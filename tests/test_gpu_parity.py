@@ -1,0 +1,328 @@
+"""GPU parity: libnbody_gb300 (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 path: per-particle relative error ||a_gpu - a_ref|| / ||a_ref|| and the
+    same for the jerk <= 1e-12 (both sides FP64; the GPU sums in a different
+    order and uses CUDA's rsqrt, so agreement is to a few ulps times the
+    conditioning sum|terms| / |sum|).
+  * mixed path: FP32 pair arithmetic (24-bit mantissa, hardware rsqrt with
+    ~2^-22.9 relative error) on FP64-resolution separations: the per-term error
+    is a few 1e-7, so the per-particle force error is bounded by a few 1e-7
+    times the conditioning; gated at 1e-6 for the 99.9th percentile and 1e-5
+    for the worst particle, with the jerk at 4x those.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1411_5234_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(x, ref):
+    return np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def gpu_force(nb, cl, eps, idx, prec, bfactor=0, G=1.0):
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, offsets=cl.offsets, eps=eps, precision=prec,
+                 bfactor=bfactor, G=G)
+    act = torch.as_tensor(np.asarray(idx, dtype=np.int32), device="cuda")
+    sim.predict(0)
+    acc, jerk, pot = sim.force(act)
+    torch.cuda.synchronize()
+    assert sim.status() == nb.NB_OK
+    out = acc.cpu().numpy(), jerk.cpu().numpy(), pot.cpu().numpy()
+    sim.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def plummer1024():
+    return inputs.plummer(1024, seed=0)
+
+
+# ------------------------------------------------------------ forces ----
+
+def test_fp64_force_config1(nb, plummer1024):
+    cl = plummer1024
+    idx = np.arange(cl.n)
+    a, j, p = gpu_force(nb, cl, 1e-4, idx, nb.NB_FP64)
+    ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4)
+    assert rel_err(a, ra).max() <= 1e-12
+    assert rel_err(j, rj).max() <= 1e-12
+    assert np.abs(p / rp - 1).max() <= 1e-13
+
+
+@pytest.mark.parametrize("n", [1000, 1027, 130])
+@pytest.mark.parametrize("m", [1, 31, 33, 257, "all"])
+@pytest.mark.parametrize("bfactor", [0, 1, 3])
+def test_fp64_force_ragged_subsets(nb, n, m, bfactor):
+    cl = inputs.plummer(n, seed=n, imf="kroupa")
+    mm = n if m == "all" else min(m, n)
+    idx = inputs.random_active(n, mm, seed=mm)
+    a, j, p = gpu_force(nb, cl, 1e-3, idx, nb.NB_FP64, bfactor)
+    ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, 1e-3, idx=idx)
+    assert rel_err(a, ra).max() <= 1e-12
+    assert rel_err(j, rj).max() <= 1e-12
+    assert np.abs(p / rp - 1).max() <= 1e-13
+
+
+@pytest.mark.parametrize("n,m", [(4099, "all"), (4099, 1), (4099, 333), (129, "all")])
+def test_mixed_force_parity(nb, n, m):
+    cl = inputs.plummer(n, seed=7, imf="kroupa")
+    mm = n if m == "all" else m
+    idx = inputs.random_active(n, mm, seed=3)
+    a, j, p = gpu_force(nb, cl, 1e-4, idx, nb.NB_MIXED)
+    ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx)
+    ea, ej = rel_err(a, ra), rel_err(j, rj)
+    assert np.quantile(ea, 0.999) <= 1e-6 and ea.max() <= 1e-5, (ea.max(), np.median(ea))
+    assert np.quantile(ej, 0.999) <= 4e-6 and ej.max() <= 4e-5, (ej.max(), np.median(ej))
+    assert np.abs(p / rp - 1).max() <= 1e-6
+
+
+def test_mixed_close_binary_resolution(nb):
+    # A hard binary (separation 1e-6) far from the origin (|x| ~ 1): plain
+    # FP32 positions would resolve the separation to ~6%; the double-single
+    # separation keeps the pair force to FP32 accuracy.
+    cl = inputs.plummer(256, seed=2)
+    pos = cl.pos.copy()
+    pos[1] = pos[0] + np.array([1e-6, 0.0, 0.0])
+    c2 = inputs.Cluster(pos, cl.vel, cl.mass, cl.offsets)
+    a, _, _ = gpu_force(nb, c2, 0.0, [0, 1], nb.NB_MIXED)
+    ra, _, _ = oracle.force(pos, cl.vel, cl.mass, 0.0, idx=[0, 1])
+    assert rel_err(a, ra).max() <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_two_body_exact_values(nb, prec):
+    # d = 3, eps = 4: |a| = G m 3 / 125, phi = -G m / 5
+    P = nb.NB_FP64 if prec == "fp64" else nb.NB_MIXED
+    tol = 1e-15 if prec == "fp64" else 3e-7
+    pos = np.array([[0.0, 0, 0], [3.0, 0, 0]])
+    cl = inputs.Cluster(pos, np.zeros((2, 3)), np.array([2.0, 5.0]), np.array([0, 2]))
+    a, j, p = gpu_force(nb, cl, 4.0, [0, 1], P, G=1.5)
+    np.testing.assert_allclose(a, [[1.5 * 5 * 3 / 125, 0, 0], [-1.5 * 2 * 3 / 125, 0, 0]],
+                               rtol=tol, atol=1e-18)
+    np.testing.assert_allclose(p, [-1.5 * 5 / 5, -1.5 * 2 / 5], rtol=tol)
+    assert np.all(j == 0.0)
+
+
+def test_bfactor_invariance(nb):
+    cl = inputs.plummer(3000, seed=5, imf="kroupa")
+    idx = inputs.random_active(3000, 200, seed=1)
+    ref = gpu_force(nb, cl, 1e-4, idx, nb.NB_FP64, 1)
+    for b in (2, 5, 16):
+        got = gpu_force(nb, cl, 1e-4, idx, nb.NB_FP64, b)
+        for x, r in zip(got[:2], ref[:2]):
+            assert rel_err(x, r).max() <= 1e-14
+    refm = gpu_force(nb, cl, 1e-4, idx, nb.NB_MIXED, 1)
+    for b in (2, 5, 16):
+        got = gpu_force(nb, cl, 1e-4, idx, nb.NB_MIXED, b)
+        for x, r in zip(got[:2], refm[:2]):
+            assert rel_err(x, r).max() <= 1e-6
+
+
+def test_force_empty_and_invalid_lists(nb, plummer1024):
+    cl = plummer1024
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nb.NB_FP64)
+    sim.predict(0)
+    empty = torch.empty(0, dtype=torch.int32, device="cuda")
+    sim.force(empty)
+    assert sim.status() == nb.NB_OK
+    bad = torch.tensor([5, 3, 9], dtype=torch.int32, device="cuda")  # not ascending
+    sim.force(bad)
+    assert sim.status() == nb.NB_EINVAL
+    sim.clear_status()
+    oob = torch.tensor([1, 2, 5000], dtype=torch.int32, device="cuda")
+    sim.force(oob)
+    assert sim.status() == nb.NB_EINVAL
+    sim.close()
+
+
+# ------------------------------------------------------------- integrator ---
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_shared_steps_config1(nb, plummer1024, prec):
+    # Plummer N = 1024, eps = 1e-4: 10 shared Hermite-4 steps of 2^-10
+    cl = plummer1024
+    P = nb.NB_FP64 if prec == "fp64" else nb.NB_MIXED
+    st = oracle.State(cl.pos, cl.vel, cl.mass, eps=1e-4, lmin=10, lmax=10)
+    for _ in range(10):
+        st.block_step()
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=P, level_min=10, level_max=10,
+                 graph_steps=4)
+    sim.step(10)
+    s = sim.get_state()
+    assert sim.status() == nb.NB_OK
+    assert np.array_equal(s["t"], st.t) and np.all(s["t"] == 10 << (40 - 10))
+    tol = 1e-12 if prec == "fp64" else 1e-7
+    assert rel_err(s["pos"], st.pos).max() <= tol
+    assert rel_err(s["vel"], st.vel).max() <= tol * 10
+    assert rel_err(s["acc"], st.acc).max() <= (1e-12 if prec == "fp64" else 1e-5)
+    assert sim.stats().block_steps == 10
+    assert sim.stats().interactions == 10 * 1024 * 1024
+    sim.close()
+
+
+def test_block_step_from_identical_state(nb):
+    cl = inputs.plummer(700, seed=4)
+    st = oracle.State(cl.pos, cl.vel, cl.mass, eps=1e-3, eta=0.01, lmin=3, lmax=20)
+    for _ in range(5):
+        st.block_step()
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-3, precision=nb.NB_FP64, eta=0.01,
+                 level_min=3, level_max=20, graph_steps=0)
+    sim.set_state(st.pos, st.vel, st.acc, st.jerk, st.t, st.level)
+    for _ in range(3):
+        before_level = st.level.copy()
+        t_next, act, dtc = st.block_step()
+        sim.step(1)
+        s = sim.get_state()
+        assert sim.status() == nb.NB_OK
+        assert np.array_equal(s["t"], st.t)           # same active set, same times
+        assert rel_err(s["pos"][act], st.pos[act]).max() <= 1e-12
+        assert rel_err(s["vel"][act], st.vel[act]).max() <= 1e-11
+        # a level may differ only where the criterion sits on a power of two
+        diff = np.flatnonzero(s["level"][act] != st.level[act])
+        for k in diff:
+            frac = math.log2(dtc[k]) - math.floor(math.log2(dtc[k]))
+            assert min(frac, 1 - frac) < 1e-9, (k, dtc[k], before_level[act[k]])
+        sim.set_state(st.pos, st.vel, st.acc, st.jerk, st.t, st.level)
+    sim.close()
+
+
+def test_block_integration_energy_drift(nb):
+    # Plummer N = 512, eps = 1e-3, levels 2^-3 .. 2^-20, t = 0 -> 1/8.  The
+    # Hermite truncation error makes the energy drift; the FP64 path must
+    # drift like the oracle running the same integrator, and the mixed path
+    # within 2x of the FP64 path.
+    cl = inputs.plummer(512, seed=8)
+    eps, t_end = 1e-3, 0.125
+    st = oracle.State(cl.pos, cl.vel, cl.mass, eps=eps, lmin=3, lmax=20)
+    e_ref0 = sum(oracle.energy(cl.pos, cl.vel, cl.mass, eps))
+    while st.time() < t_end:
+        st.block_step()
+    assert np.all(st.t == st.t[0])
+    d_ref = sum(oracle.energy(st.pos, st.vel, st.mass, eps)) / e_ref0 - 1
+    drift = {}
+    for P in (nb.NB_FP64, nb.NB_MIXED):
+        sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=eps, precision=P, level_min=3, level_max=20)
+        e0 = sum(sim.energy())
+        assert abs(e0 / e_ref0 - 1) < 1e-12
+        sim.set_end_time(sim.ticks(t_end))
+        for _ in range(200):
+            sim.step(256)
+            if sim.stats().t_min == sim.ticks(t_end):
+                break
+        stats = sim.stats()
+        assert stats.t_min == stats.t_max == sim.ticks(t_end)
+        s = sim.get_state()
+        assert np.all(s["t"] == sim.ticks(t_end))
+        drift[P] = sum(sim.energy()) / e0 - 1
+        assert sim.status() == nb.NB_OK
+        sim.close()
+    assert abs(d_ref) < 1e-5
+    assert abs(drift[nb.NB_FP64] - d_ref) <= 0.05 * abs(d_ref) + 1e-9, (drift, d_ref)
+    assert abs(drift[nb.NB_MIXED]) <= 2 * abs(drift[nb.NB_FP64]) + 1e-9, (drift, d_ref)
+
+
+def test_graphs_match_direct_launches(nb):
+    cl = inputs.plummer(600, seed=9)
+    out = []
+    for g in (0, 5):
+        sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-3, precision=nb.NB_MIXED, level_min=3,
+                     level_max=20, graph_steps=g)
+        sim.step(23)
+        out.append(sim.get_state())
+        sim.close()
+    for k in ("pos", "vel", "t", "level"):
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_checkpoint_resume_bitwise(nb):
+    cl = inputs.plummer(400, seed=10)
+    kw = dict(eps=1e-3, precision=nb.NB_FP64, level_min=3, level_max=20)
+    a = nb.Sim(cl.pos, cl.vel, cl.mass, **kw)
+    a.step(40)
+    ref = a.get_state()
+    b = nb.Sim(cl.pos, cl.vel, cl.mass, **kw)
+    b.step(20)
+    mid = b.get_state()
+    b.close()
+    c = nb.Sim(cl.pos, cl.vel, cl.mass, **kw)
+    c.set_state(mid["pos"], mid["vel"], mid["acc"], mid["jerk"], mid["t"], mid["level"])
+    c.step(20)
+    got = c.get_state()
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+    a.close()
+    c.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_clusters_alone(nb, prec):
+    P = nb.NB_FP64 if prec == "fp64" else nb.NB_MIXED
+    parts = [inputs.plummer(n, seed=s) for n, s in ((300, 1), (517, 2), (64, 3))]
+    pos = np.concatenate([p.pos for p in parts])
+    vel = np.concatenate([p.vel for p in parts])
+    mass = np.concatenate([p.mass for p in parts])
+    off = np.array([0, 300, 817, 881])
+    kw = dict(eps=1e-3, precision=P, level_min=3, level_max=20, bfactor=1)
+    batch = nb.Sim(pos, vel, mass, offsets=off, **kw)
+    batch.step(30)
+    sb = batch.get_state()
+    for k, p in enumerate(parts):
+        alone = nb.Sim(p.pos, p.vel, p.mass, **kw)
+        alone.step(30)
+        sa = alone.get_state()
+        for key in ("pos", "vel", "acc", "jerk", "t", "level"):
+            assert np.array_equal(sa[key], sb[key][off[k]:off[k + 1]]), (k, key)
+        ek, ep = batch.energy(k)
+        ea = alone.energy()
+        assert ek == pytest.approx(ea[0], rel=1e-14) and ep == pytest.approx(ea[1], rel=1e-13)
+        alone.close()
+    batch.close()
+
+
+def test_energy_matches_oracle(nb):
+    cl = inputs.plummer_batch(3, 100, 400, seed0=5)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, offsets=cl.offsets, eps=1e-4, precision=nb.NB_MIXED)
+    tot = [0.0, 0.0]
+    for k in range(3):
+        lo, hi = cl.offsets[k], cl.offsets[k + 1]
+        ek, ep = sim.energy(k)
+        rk, rp = oracle.energy(cl.pos[lo:hi], cl.vel[lo:hi], cl.mass[lo:hi], 1e-4)
+        assert ek == pytest.approx(rk, rel=1e-13) and ep == pytest.approx(rp, rel=1e-12)
+        tot[0] += rk
+        tot[1] += rp
+    ek, ep = sim.energy(-1)
+    assert ek == pytest.approx(tot[0], rel=1e-13) and ep == pytest.approx(tot[1], rel=1e-12)
+    sim.close()
+
+
+def test_invalid_arguments(nb):
+    cl = inputs.plummer(64, seed=0)
+    with pytest.raises(nb.NBError) as e:
+        nb.Sim(cl.pos, cl.vel, -cl.mass)
+    assert e.value.code == nb.NB_EINVAL
+    with pytest.raises(nb.NBError):
+        nb.Sim(cl.pos, cl.vel, cl.mass, offsets=np.array([0, 40, 40, 64]))
+    bad_pos = cl.pos.copy()
+    bad_pos[3, 1] = np.nan
+    with pytest.raises(nb.NBError):
+        nb.Sim(bad_pos, cl.vel, cl.mass)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, precision=nb.NB_FP64, level_min=3, level_max=10)
+    s = sim.get_state()
+    lv = s["level"].copy()
+    lv[0] = 11
+    with pytest.raises(nb.NBError):
+        sim.set_state(s["pos"], s["vel"], s["acc"], s["jerk"], s["t"], lv)
+    # a correction must move forward in time
+    act = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    a = torch.zeros((2, 3), dtype=torch.float64, device="cuda")
+    sim.correct(0, act, a, a)
+    assert sim.status() == nb.NB_EINVAL
+    sim.close()
