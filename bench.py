@@ -58,7 +58,40 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--kernel-case", choices=["mixed", "fp64"], default=None,
+                   help="run only nb_force on m random targets of N (profiling case)")
+    p.add_argument("--m", type=int, default=16384)
     return p.parse_args()
+
+
+def kernel_case(args):
+    """nb_force alone (W + K launches) on m random targets of the N-body workload."""
+    import torch
+    from paper_1411_5234_gb300 import inputs, nbody
+    torch.cuda.set_device(0)
+    cl = make_cluster(args.n, 0)
+    prec = nbody.NB_MIXED if args.kernel_case == "mixed" else nbody.NB_FP64
+    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=prec, graph_steps=0)
+    sim.predict(0)
+    act = torch.as_tensor(inputs.random_active(cl.n, args.m, seed=1), device="cuda")
+    acc = torch.empty((args.m, 3), dtype=torch.float64, device="cuda")
+    jerk = torch.empty_like(acc)
+    for _ in range(args.warmup):
+        sim.force(act, acc, jerk, None, want_pot=False)
+    sim.synchronize()
+    sim.profile(True)
+    for _ in range(args.steps):
+        sim.force(act, acc, jerk, None, want_pot=False)
+    ms, cnt = sim.profile_read()
+    assert sim.status() == nbody.NB_OK
+    per = ms / max(cnt, 1)
+    rate = args.m * cl.n / (per * 1e-3)
+    print(json.dumps({"kernel_case": args.kernel_case, "N": cl.n, "m": args.m,
+                      "ms_per_launch": per, "interactions_per_s": rate,
+                      "frac_fp32_peak_38": FLOPS_PER_INTERACTION * rate
+                      / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6)}), flush=True)
+    sim.close()
+    return 0
 
 
 def workload_config(n):
@@ -213,6 +246,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_case:
+        return kernel_case(args)
 
     import torch
     from paper_1411_5234_gb300 import inputs, nbody
