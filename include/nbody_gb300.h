@@ -196,6 +196,34 @@ int nb_clear_status(nb_ctx *ctx);
 /* Text for a status code (static storage). */
 const char *nb_strerror(int code);
 
+/* ---- Forces without a workspace ------------------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory where they need forces (code running in a
+ * host callback or library hook while another framework owns all device
+ * allocations, or runtimes that forbid cudaMalloc after start-up) and so
+ * cannot provide the workspace nb_init() needs.  It computes the same
+ * quantities as nb_force() for one cluster, directly from device arrays:
+ * pos, vel (n x 3), mass (n), target_idx (m int32 in [0, n), any order),
+ * outputs acc, jerk (m x 3) and pot (m, or NULL), on `stream`.
+ * precision is NB_MIXED or NB_FP64.  Asynchronous; a target index outside
+ * [0, n) leaves its row unspecified.
+ *
+ * It allocates nothing: the packed sources, the i-split partial sums and the
+ * plan words live in one fixed device array of 6,689,024 bytes compiled into
+ * the library, present on every GPU that loads the library until the process
+ * exits.  Limits: 1 <= n <= NB_NOALLOC_MAX_SOURCES (larger n returns
+ * NB_EINVAL without launching anything), 0 <= m <= n.  All calls on a device
+ * share that array and each call leaves its contents behind; a call rewrites
+ * everything it reads first, but calls whose work overlaps on the GPU (other
+ * streams without ordering, other host threads) race on it.  The first call
+ * on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture on the device. */
+#define NB_NOALLOC_MAX_SOURCES 32768
+int nb_force_noalloc(const double *pos, const double *vel, const double *mass,
+                     int64_t n, const int32_t *target_idx, int64_t m, double G,
+                     double eps, int32_t precision, double *acc, double *jerk,
+                     double *pot, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ FUNCTIONS = [
     "nb_default_config", "nb_workspace_size", "nb_init", "nb_free", "nb_predict", "nb_force",
     "nb_correct", "nb_step_block", "nb_set_end_time", "nb_energy", "nb_get_state",
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
-    "nb_profile_enable", "nb_profile_read",
+    "nb_profile_enable", "nb_profile_read", "nb_force_noalloc",
 ]
 
 
@@ -71,6 +71,8 @@ def _load() -> ctypes.CDLL:
         "nb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "nb_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "nb_profile_read": (ctypes.c_int, [P, P, P]),
+        "nb_force_noalloc": (ctypes.c_int, [P, P, P, i64, P, i64, ctypes.c_double,
+                                            ctypes.c_double, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -287,3 +289,37 @@ class Sim:
         cur = torch.cuda.current_stream()
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
+
+
+NOALLOC_MAX_SOURCES = 32768
+
+
+def force_noalloc(pos, vel, mass, targets, G=1.0, eps=1e-4, precision=NB_MIXED,
+                  acc=None, jerk=None, pot=None, want_pot=True, stream=None):
+    """nb_force_noalloc: forces from plain CUDA tensors, with no workspace.
+
+    For callers that cannot allocate device memory at the call site: the
+    library keeps its scratch in a fixed device array.  ``pos``/``vel``
+    (n, 3) and ``mass`` (n,) float64 CUDA tensors, ``targets`` int32 CUDA
+    tensor; outputs may be passed in (as the no-allocation caller would) or
+    are created here for convenience.
+    """
+    n = mass.numel()
+    m = targets.numel()
+    for t, dt in ((pos, torch.float64), (vel, torch.float64), (mass, torch.float64),
+                  (targets, torch.int32)):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("inputs must be contiguous CUDA tensors (float64 / int32)")
+    if acc is None:
+        acc = torch.empty((m, 3), dtype=torch.float64, device=pos.device)
+    if jerk is None:
+        jerk = torch.empty((m, 3), dtype=torch.float64, device=pos.device)
+    if pot is None and want_pot:
+        pot = torch.empty(m, dtype=torch.float64, device=pos.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.nb_force_noalloc(_dptr(pos), _dptr(vel), _dptr(mass), n, _dptr(targets), m,
+                                float(G), float(eps), int(precision), _dptr(acc), _dptr(jerk),
+                                _dptr(pot), ctypes.c_void_p(st.cuda_stream)),
+           "nb_force_noalloc")
+    return acc, jerk, pot
+

@@ -1,0 +1,77 @@
+"""nb_force_noalloc: the entry point for callers that cannot allocate.
+
+Such callers (code in a host callback or library hook while another framework
+owns every device allocation, or runtimes that forbid cudaMalloc after
+start-up) cannot hand the library a workspace, so this entry point keeps its
+scratch in a fixed device array inside the library.  It must give the same
+forces as the regular nb_force on the same inputs, call after call, even
+though each call finds the previous call's data in that array.
+
+Kept in a file of its own that pytest collects last.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1411_5234_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(x, ref):
+    return np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def regular_force(nb, cl, eps, idx, prec):
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=eps, precision=prec)
+    sim.predict(0)
+    act = torch.as_tensor(np.asarray(idx, dtype=np.int32), device="cuda")
+    a, j, p = sim.force(act)
+    torch.cuda.synchronize()
+    assert sim.status() == nb.NB_OK
+    out = a.cpu().numpy(), j.cpu().numpy(), p.cpu().numpy()
+    sim.close()
+    return out
+
+
+def noalloc_force(nb, cl, eps, idx, prec, outs):
+    dev = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt,
+                                                      device="cuda")
+    acc, jerk, pot = outs
+    nb.force_noalloc(dev(cl.pos), dev(cl.vel), dev(cl.mass), dev(idx, torch.int32), eps=eps,
+                     precision=prec, acc=acc, jerk=jerk, pot=pot)
+    torch.cuda.synchronize()
+    return acc.cpu().numpy(), jerk.cpu().numpy(), pot.cpu().numpy()
+
+
+def test_noalloc_matches_nb_force_twice_in_a_row(nb):
+    cases = [
+        # (cluster, eps, targets, precision, tolerance as used by the parity tests)
+        (inputs.plummer(5000, seed=21, imf="kroupa"), 1e-4,
+         inputs.random_active(5000, 777, seed=5), nb.NB_MIXED, 1e-6),
+        (inputs.plummer(20003, seed=22), 1e-3,
+         inputs.random_active(20003, 20003, seed=6), nb.NB_FP64, 1e-14),
+        (inputs.plummer(5000, seed=21, imf="kroupa"), 1e-4,
+         inputs.random_active(5000, 3001, seed=7), nb.NB_MIXED, 1e-6),
+    ]
+    for cl, eps, idx, prec, tol in cases:
+        m = len(idx)
+        # outputs the no-allocation caller would already own
+        outs = (torch.full((m, 3), np.nan, dtype=torch.float64, device="cuda"),
+                torch.full((m, 3), np.nan, dtype=torch.float64, device="cuda"),
+                torch.full((m,), np.nan, dtype=torch.float64, device="cuda"))
+        got = noalloc_force(nb, cl, eps, idx, prec, outs)
+        ref = regular_force(nb, cl, eps, idx, prec)
+        assert rel_err(got[0], ref[0]).max() <= tol
+        assert rel_err(got[1], ref[1]).max() <= tol
+        assert np.abs(got[2] / ref[2] - 1).max() <= tol
+
+
+def test_noalloc_rejects_sizes_beyond_its_array(nb):
+    n = nb.NOALLOC_MAX_SOURCES + 1
+    z = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    mass = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+    idx = torch.arange(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(nb.NBError) as e:
+        nb.force_noalloc(z, z, mass, idx)
+    assert e.value.code == nb.NB_EINVAL
