@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--kernel-case", choices=["mixed", "fp64"], default=None,
                    help="run only nb_force on m random targets of N (profiling case)")
     p.add_argument("--m", type=int, default=16384)
+    p.add_argument("--variant", type=int, default=None, help="mixed force kernel shape")
     return p.parse_args()
 
 
@@ -71,7 +72,8 @@ def kernel_case(args):
     torch.cuda.set_device(0)
     cl = make_cluster(args.n, 0)
     prec = nbody.NB_MIXED if args.kernel_case == "mixed" else nbody.NB_FP64
-    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=prec, graph_steps=0)
+    kw = {} if args.variant is None else {"variant": args.variant}
+    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=prec, graph_steps=0, **kw)
     sim.predict(0)
     act = torch.as_tensor(inputs.random_active(cl.n, args.m, seed=1), device="cuda")
     acc = torch.empty((args.m, 3), dtype=torch.float64, device="cuda")
@@ -86,7 +88,8 @@ def kernel_case(args):
     assert sim.status() == nbody.NB_OK
     per = ms / max(cnt, 1)
     rate = args.m * cl.n / (per * 1e-3)
-    print(json.dumps({"kernel_case": args.kernel_case, "N": cl.n, "m": args.m,
+    print(json.dumps({"kernel_case": args.kernel_case, "variant": sim.cfg.variant,
+                      "N": cl.n, "m": args.m,
                       "ms_per_launch": per, "interactions_per_s": rate,
                       "frac_fp32_peak_38": FLOPS_PER_INTERACTION * rate
                       / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6)}), flush=True)

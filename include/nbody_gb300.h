@@ -87,11 +87,17 @@ typedef struct {
     int32_t precision;  /* nb_precision                                        */
     int32_t bfactor;    /* i-split factor B: 0 = chosen per step by the plan   */
     int32_t graph_steps;/* block steps captured per CUDA graph (0 = no graph)  */
-    int32_t reserved[2];
+    int32_t sort_sources;/* 1: force sources kept in spatial (Morton) order of
+                            the initial positions, 0: in particle order.  Only
+                            speed depends on it, never the results' accuracy. */
+    int32_t variant;    /* shape of the mixed force kernel, 0..3 (see
+                           nb_force_mixed.cu); all give results of the same
+                           accuracy */
 } nb_config;
 
 /* Defaults: G = 1, eps = 1e-4, eta = 0.01, eta_start = 0.01, level_min = 0,
- * level_max = 30, tick_exp = 40, NB_MIXED, bfactor = 0, graph_steps = 16. */
+ * level_max = 30, tick_exp = 40, NB_MIXED, bfactor = 0, graph_steps = 16,
+ * sort_sources = 1, variant = 1. */
 void nb_default_config(nb_config *cfg);
 
 /* Bytes of the device workspace for n_total particles in n_clusters clusters
@@ -209,7 +215,7 @@ const char *nb_strerror(int code);
  * [0, n) leaves its row unspecified.
  *
  * It allocates nothing: the packed sources, the i-split partial sums and the
- * plan words live in one fixed device array of 6,689,024 bytes compiled into
+ * plan words live in one fixed device array of 6,697,472 bytes compiled into
  * the library, present on every GPU that loads the library until the process
  * exits.  Limits: 1 <= n <= NB_NOALLOC_MAX_SOURCES (larger n returns
  * NB_EINVAL without launching anything), 0 <= m <= n.  All calls on a device

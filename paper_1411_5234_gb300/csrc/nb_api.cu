@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/nbody_gb300.h"
@@ -22,8 +23,8 @@ constexpr int kEnergyBlocks = 304;
 struct Layout {
   size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
       src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, bfac, esum,
-      status, counters, t_end, total;
-  int64_t S, part_items;
+      status, counters, t_end, tiles, toff, sperm, sinv, total;
+  int64_t S, part_items, n_tiles;
 };
 
 size_t take(size_t& cur, size_t bytes) {
@@ -32,9 +33,10 @@ size_t take(size_t& cur, size_t bytes) {
   return o;
 }
 
-Layout make_layout(int64_t N, int32_t K, int64_t S) {
+Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
   Layout L{};
   L.S = S;
+  L.n_tiles = n_tiles;
   const int64_t nitile = ceil_div64(N, kF64NI) + K;
   L.part_items = 2 * nitile > 2048 ? 2 * nitile : 2048;
   const size_t ni_max = kMixNI > kF64NI ? kMixNI : kF64NI;
@@ -53,7 +55,7 @@ Layout make_layout(int64_t N, int32_t K, int64_t S) {
   L.src64_pos = take(c, 32 * S);
   L.src64_vel = take(c, 32 * S);
   L.partials = take(c, (size_t)L.part_items * kPartialComps * ni_max * 8);
-  L.blk_count = take(c, 4 * ((size_t)scan_blocks(N) + 1));
+  L.blk_count = take(c, 4 * ((size_t)n_tiles + 1));
   L.off = take(c, 8 * ((size_t)K + 1));
   L.soff = take(c, 8 * ((size_t)K + 1));
   L.t_cur = take(c, 8 * (size_t)K);
@@ -65,6 +67,10 @@ Layout make_layout(int64_t N, int32_t K, int64_t S) {
   L.status = take(c, 4);
   L.counters = take(c, 8 * 4);
   L.t_end = take(c, 8);
+  L.tiles = take(c, 32 * (size_t)n_tiles);
+  L.toff = take(c, 4 * ((size_t)K + 1));
+  L.sperm = take(c, 4 * (size_t)S);
+  L.sinv = take(c, 4 * (size_t)N);
   L.total = c;
   return L;
 }
@@ -78,6 +84,8 @@ bool config_ok(const nb_config* c) {
   if (c->level_min < 0 || c->level_min > c->level_max || c->level_max > c->tick_exp) return false;
   if (c->precision != NB_FP64 && c->precision != NB_MIXED) return false;
   if (c->bfactor < 0 || c->graph_steps < 0) return false;
+  if (c->sort_sources != 0 && c->sort_sources != 1) return false;
+  if (c->variant < 0 || c->variant >= force_mixed_variants()) return false;
   return true;
 }
 
@@ -85,6 +93,61 @@ int64_t slots_of(const int64_t* off, int32_t K) {
   int64_t S = 0;
   for (int32_t k = 0; k < K; ++k) S += round_up64(off[k + 1] - off[k], 4);
   return S;
+}
+
+int64_t tiles_of(const int64_t* off, int32_t K) {
+  int64_t n = 0;
+  for (int32_t k = 0; k < K; ++k) n += ceil_div64(round_up64(off[k + 1] - off[k], 4), kMixJT);
+  return n;
+}
+
+// 3-D Morton (Z-order) key of a point quantised to 21 bits per axis.
+uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+// Source slots of every cluster: particles in Morton order of their positions
+// (pos: n x 3 host), or in particle order when `sorted` is false.  Pad slots
+// get -1.  sperm: S entries, sinv: N entries.
+void source_order(const double* pos, const int64_t* off, int32_t K, const int64_t* soff,
+                  bool sorted, std::vector<int32_t>& sperm, std::vector<int32_t>& sinv) {
+  for (int32_t k = 0; k < K; ++k) {
+    const int64_t n0 = off[k], nk = off[k + 1] - off[k];
+    std::vector<std::pair<uint64_t, int64_t>> key(nk);
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nk; ++i)
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(lo[c], pos[3 * (n0 + i) + c]);
+        hi[c] = std::max(hi[c], pos[3 * (n0 + i) + c]);
+      }
+    double span = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+    for (int64_t i = 0; i < nk; ++i) {
+      uint64_t code = 0;
+      if (sorted) {
+        for (int c = 0; c < 3; ++c) {
+          double q = (pos[3 * (n0 + i) + c] - lo[c]) / span * 2097151.0;
+          uint64_t u = (uint64_t)std::min(std::max(q, 0.0), 2097151.0);
+          code |= spread3(u) << c;
+        }
+      }
+      key[i] = {code, i};
+    }
+    if (sorted) std::sort(key.begin(), key.end());
+    for (int64_t r = 0; r < round_up64(nk, 4); ++r) {
+      if (r < nk) {
+        sperm[soff[k] + r] = static_cast<int32_t>(n0 + key[r].second);
+        sinv[n0 + key[r].second] = static_cast<int32_t>(soff[k] + r);
+      } else {
+        sperm[soff[k] + r] = -1;
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -127,6 +190,9 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, double* acc, int sa, doub
   a.act_off = c->d.act_off;
   a.item_off = c->d.item_off;
   a.bfac = c->d.bfac;
+  a.sinv = c->d.sinv;
+  a.tiles = c->d.tiles;
+  a.toff = c->d.toff;
   a.K = c->d.K;
   if (f64_sources) {
     a.src_a = c->d.src64_pos;
@@ -221,7 +287,7 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, double* acc, int sa,
   if (f64)
     e = launch_force_fp64(fa, c->grid_f64, pot_only ? kF64PotOnly : kF64Full, c->st);
   else
-    e = launch_force_mixed(fa, c->grid_mix, pot != nullptr, c->st);
+    e = launch_force_mixed(fa, c->grid_mix, pot != nullptr, c->cfg.variant, c->st);
   if (e != cudaSuccess) return e;
   if (c->prof) {
     e = cudaEventRecord(ev.second, c->st);
@@ -242,7 +308,8 @@ cudaError_t enqueue_block_step(nb_ctx* c) {
   if (e != cudaSuccess) return e;
   double* an = reinterpret_cast<double*>(c->d.acc_new);
   double* jn = reinterpret_cast<double*>(c->d.jerk_new);
-  e = enqueue_force(c, c->d.active, an, 4, jn, 4, an + 3, 4, f64, 1, 1, false, c->d.N);
+  // the integrator needs no potential: the force kernel skips it here
+  e = enqueue_force(c, c->d.active, an, 4, jn, 4, nullptr, 0, f64, 1, 1, false, c->d.N);
   if (e != cudaSuccess) return e;
   CorrectArgs ca{};
   ca.active = c->d.active;
@@ -251,8 +318,8 @@ cudaError_t enqueue_block_step(nb_ctx* c) {
   ca.sa = 4;
   ca.jerk = jn;
   ca.sj = 4;
-  ca.pot = an + 3;
-  ca.sp = 4;
+  ca.pot = nullptr;
+  ca.sp = 0;
   ca.t_tgt = c->d.t_cur;
   ca.eta = c->cfg.eta;
   ca.T = T;
@@ -295,14 +362,18 @@ void nb_default_config(nb_config* cfg) {
   cfg->precision = NB_MIXED;
   cfg->bfactor = 0;
   cfg->graph_steps = 16;
+  cfg->sort_sources = 1;
+  cfg->variant = 1;
 }
 
 int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config* cfg, size_t* bytes) {
   if (!bytes || !config_ok(cfg) || n_clusters < 1 || n_total < n_clusters ||
       n_total > (int64_t)INT32_MAX - 1024)
     return NB_EINVAL;
-  // worst case of the slot padding: 3 pad slots per cluster
-  *bytes = make_layout(n_total, n_clusters, n_total + 3 * (int64_t)n_clusters).total;
+  // worst case of the slot padding (3 pad slots per cluster) and of the
+  // tile count (one partial tile per cluster)
+  const int64_t S = n_total + 3 * (int64_t)n_clusters;
+  *bytes = make_layout(n_total, n_clusters, S, S / kMixJT + n_clusters).total;
   return NB_OK;
 }
 
@@ -332,7 +403,8 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   c->off_host.assign(offsets, offsets + n_clusters + 1);
   c->mass_host.assign(mass, mass + N);
   const int64_t S = slots_of(offsets, n_clusters);
-  c->L = make_layout(N, n_clusters, S);
+  const int64_t n_tiles = tiles_of(offsets, n_clusters);
+  c->L = make_layout(N, n_clusters, S, n_tiles);
   char* w = static_cast<char*>(workspace);
   Dev& d = c->d;
   d.N = N;
@@ -365,6 +437,11 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   d.status = reinterpret_cast<uint32_t*>(w + c->L.status);
   d.counters = reinterpret_cast<unsigned long long*>(w + c->L.counters);
   d.t_end = reinterpret_cast<int64_t*>(w + c->L.t_end);
+  d.tiles = reinterpret_cast<float4*>(w + c->L.tiles);
+  d.toff = reinterpret_cast<int32_t*>(w + c->L.toff);
+  d.n_tiles = n_tiles;
+  d.sperm = reinterpret_cast<int32_t*>(w + c->L.sperm);
+  d.sinv = reinterpret_cast<int32_t*>(w + c->L.sinv);
 
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -372,17 +449,21 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
     delete c;
     return NB_ECUDA;
   }
-  c->grid_mix = sms * force_mixed_ctas_per_sm();
+  c->grid_mix = sms * force_mixed_ctas_per_sm(cfg->variant);
   c->grid_f64 = sms * force_fp64_ctas_per_sm();
 
   // host staging of the initial state
   std::vector<double> p4(4 * N), v4(4 * N, 0.0);
   std::vector<int32_t> cid(N);
   std::vector<int64_t> soff(n_clusters + 1, 0);
+  std::vector<int32_t> toff(n_clusters + 1, 0);
   for (int32_t k = 0; k < n_clusters; ++k) {
     soff[k + 1] = soff[k] + round_up64(offsets[k + 1] - offsets[k], 4);
+    toff[k + 1] = toff[k] + static_cast<int32_t>(ceil_div64(soff[k + 1] - soff[k], kMixJT));
     for (int64_t i = offsets[k]; i < offsets[k + 1]; ++i) cid[i] = k;
   }
+  std::vector<int32_t> sperm(S), sinv(N);
+  source_order(pos, offsets, n_clusters, soff.data(), cfg->sort_sources != 0, sperm, sinv);
   for (int64_t i = 0; i < N; ++i) {
     p4[4 * i] = pos[3 * i];
     p4[4 * i + 1] = pos[3 * i + 1];
@@ -401,6 +482,9 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
         cudaMemcpyAsync(d.cid, cid.data(), 4 * N, cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(d.off, offsets, 8 * (n_clusters + 1), cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(d.soff, soff.data(), 8 * (n_clusters + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(d.toff, toff.data(), 4 * (n_clusters + 1), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(d.sperm, sperm.data(), 4 * S, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(d.sinv, sinv.data(), 4 * N, cudaMemcpyHostToDevice, st) ||
         cudaMemsetAsync(d.acc, 0, 32 * N, st) || cudaMemsetAsync(d.jerk, 0, 32 * N, st) ||
         cudaMemsetAsync(d.t, 0, 8 * N, st) || cudaMemsetAsync(d.level, 0, 4 * N, st) ||
         cudaMemsetAsync(d.t_cur, 0, 8 * n_clusters, st) ||
@@ -408,8 +492,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
       rc = NB_ECUDA;
       break;
     }
-    if (launch_fill_i64(d.t_min, n_clusters, big, st) || launch_fill_i64(d.t_end, 1, big, st) ||
-        launch_init_pads(d, st)) {
+    if (launch_fill_i64(d.t_min, n_clusters, big, st) || launch_fill_i64(d.t_end, 1, big, st)) {
       rc = NB_ECUDA;
       break;
     }

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_force_fp64(const ForceArgs a) {
         valid = false;
         atomicOr(a.status, kStatusInval);
       } else {
-        s.slot = sk0 + (p - p0);
+        s.slot = a.sinv ? (int64_t)a.sinv[p] : sk0 + (p - p0);
         const dbl4 ip = gp[s.slot];
         s.x = ip.x; s.y = ip.y; s.z = ip.z;
         if (MODE == kF64Full) {

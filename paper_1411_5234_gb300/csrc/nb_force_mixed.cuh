@@ -1,0 +1,434 @@
+// nb_force_mixed.cuh -- mixed-precision direct-summation force kernel (sm_103a),
+// templated on its shape.
+//
+// Computes, for each target i, Eq. 1 with the softening of Eq. 2 plus the
+// jerk and potential:
+//   a_i  =  sum_j m_j d / s^3,   jerk_i = sum_j m_j (w / s^3 - 3 (d.w) d / s^5),
+//   pot_i = -sum_j m_j / s,       d = r_j - r_i, w = v_j - v_i, s^2 = d.d + eps^2
+// (G applied on output).
+//
+// Precision (Sec. 2 item 4: DP resolution for the separations and the sums,
+// SP for the rest, square roots included).  Sources are stored relative to
+// the centre c_J of their tile of kMixJT spatially sorted slots, as
+// double-single offsets delta_j = dh_j + dl_j; a target's position relative to
+// the centre, e = c_J - r_i, is formed per tile in double-single (eh + el).
+//   * near tiles (some target of the warp within 2.5 tile radii h_J of c_J,
+//     the own tile included): d = (dh_j + eh) + (dl_j + el), FP64-like
+//     resolution for close pairs;
+//   * far tiles (every target of the warp beyond 2.5 h_J): d = dh_j + eh.
+//     With |e| >= 2 h_J, |d| >= |e| - h_J >= max(h_J, |e| / 2), so the three
+//     roundings (of dh_j, of eh, of the sum) stay within 4 units of 2^-24 |d|:
+//     the separation keeps the relative accuracy of the FP32 arithmetic
+//     after it, without the cancellation that absolute FP32 positions suffer.
+// Everything after the separation is FP32 (hardware rsqrt and reciprocal);
+// sums are accumulated per tile in FP32 and folded into a compensated
+// (hi, lo) FP32 pair per tile (two-sum), then combined in FP64.
+//
+// GB300 mapping:
+//   * persistent CTAs loop over work items (cluster, i-tile, j-chunk); the
+//     j-chunk split is the i-splitting of Sec. 2 item 3 (Bfactor): B chunks
+//     of the source range per i-tile, partial sums reduced afterwards in a
+//     fixed order;
+//   * source tiles and their (centre, radius) record are staged in shared
+//     memory (Sec. 2 item 5) by bulk copies (TMA engine, cp.async.bulk) into a
+//     two-stage ring guarded by mbarriers; waits are bounded and report
+//     NB_ETIMEOUT instead of hanging;
+//   * every pair operation is a packed f32x2 instruction over two sources,
+//     feeding the FP32 pipe at full width; IPT targets per thread share each
+//     shared-memory load.
+//
+// Shape parameters (MixShape): NT threads per CTA, IPT targets per thread
+// (NT * IPT == kMixNI), POT computes the potential, RCP takes 1/s^2 from the
+// SFU reciprocal instead of an FP32 multiply, SMT keeps the compensated
+// totals in shared memory instead of registers, UNR unrolls the source loop,
+// MINB is the CTAs-per-SM hint of __launch_bounds__.
+#pragma once
+#include "nb_internal.cuh"
+
+namespace nb {
+namespace mixk {
+
+constexpr int JT = kMixJT;
+constexpr int kGroupF4 = 10;                      // float4 per group of 4 sources
+constexpr int kTileF4 = JT / 4 * kGroupF4;        // float4 per tile
+constexpr uint32_t kGroupBytes = kGroupF4 * 16;
+constexpr float kFarRatio2 = 2.5f * 2.5f;         // far: |e|^2 > (2.5 h)^2
+
+// component order inside a group of 4 sources (float4 index)
+enum { cDXH = 0, cDYH, cDZH, cM, cVX, cVY, cVZ, cDXL, cDYL, cDZL };
+
+template <int NT_, int IPT_, bool POT_, bool RCP_, bool SMT_, int UNR_, int MINB_>
+struct MixShape {
+  static constexpr int NT = NT_, IPT = IPT_, NI = NT_ * IPT_, UNR = UNR_, MINB = MINB_;
+  static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_;
+  static_assert(NT_ * IPT_ == kMixNI, "targets per work item are fixed");
+};
+
+struct Target {
+  float xh, yh, zh, xl, yl, zl;                     // r_i, double-single
+  f2 nvx, nvy, nvz;                                 // -v_i as broadcast pairs
+  f2 ex, ey, ez;                                    // hi part of c_J - r_i (broadcast)
+  f2 ax, ay, az, j1x, j1y, j1z, j2x, j2y, j2z, pt;  // per-tile sums (2 lanes)
+  int64_t slot;
+};
+
+__device__ __forceinline__ f2 bcast(float v) { return f2_pack(v, v); }
+
+// (ah + al) - (bh + bl) in double-single, renormalised.
+__device__ __forceinline__ void ds_sub(float ah, float al, float bh, float bl, float& rh,
+                                       float& rl) {
+  const float s = ah - bh;
+  const float bb = s - ah;
+  float err = (ah - (s - bb)) + (-bh - bb);
+  err += al - bl;
+  rh = s + err;
+  rl = err - (rh - s);
+}
+
+// Shared tail of one pair step: from the separation d, relative velocity w
+// to the accumulators.
+template <class Sh, bool MASK>
+__device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx, f2 wy, f2 wz,
+                                          f2 m, f2 eps2, int64_t js) {
+  f2 r2 = f2_fma(dx, dx, eps2);
+  r2 = f2_fma(dy, dy, r2);
+  r2 = f2_fma(dz, dz, r2);
+  f2 rv = f2_mul(dx, wx);
+  rv = f2_fma(dy, wy, rv);
+  rv = f2_fma(dz, wz, rv);
+  const float2 q = f2_unpack(r2);
+  float ri0 = rsqrt_approx(q.x);
+  float ri1 = rsqrt_approx(q.y);
+  float rr0 = 0.f, rr1 = 0.f;
+  if (Sh::RCP) {
+    rr0 = rcp_approx(q.x);
+    rr1 = rcp_approx(q.y);
+  }
+  if (MASK) {  // j == i is excluded by index (Eq. 1)
+    if (js == s.slot) ri0 = rr0 = 0.f;
+    if (js + 1 == s.slot) ri1 = rr1 = 0.f;
+  }
+  const f2 rinv = f2_pack(ri0, ri1);
+  const f2 r2inv = Sh::RCP ? f2_pack(rr0, rr1) : f2_mul(rinv, rinv);
+  const f2 mri = f2_mul(m, rinv);
+  const f2 mr3 = f2_mul(mri, r2inv);
+  if (Sh::POT) s.pt = f2_add(s.pt, mri);
+  const f2 u = f2_mul(rv, r2inv);
+  const f2 bb = f2_mul(u, mr3);
+  s.ax = f2_fma(mr3, dx, s.ax);
+  s.ay = f2_fma(mr3, dy, s.ay);
+  s.az = f2_fma(mr3, dz, s.az);
+  s.j1x = f2_fma(mr3, wx, s.j1x);
+  s.j1y = f2_fma(mr3, wy, s.j1y);
+  s.j1z = f2_fma(mr3, wz, s.j1z);
+  s.j2x = f2_fma(bb, dx, s.j2x);
+  s.j2y = f2_fma(bb, dy, s.j2y);
+  s.j2z = f2_fma(bb, dz, s.j2z);
+}
+
+// Far tile: d = dh_j + eh.
+template <class Sh>
+__device__ __forceinline__ void tile_far(const float4* __restrict__ tile, int ngroups,
+                                         Target (&tg)[Sh::IPT], f2 eps2) {
+#pragma unroll Sh::UNR
+  for (int g = 0; g < ngroups; ++g) {
+    const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
+    const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
+                     vy = G[cVY], vz = G[cVZ];
+#pragma unroll
+    for (int r = 0; r < Sh::IPT; ++r) {
+      Target& s = tg[r];
+      pair_tail<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
+                           f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
+                           eps2, 0);
+      pair_tail<Sh, false>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
+                           f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
+                           eps2, 0);
+    }
+  }
+}
+
+// Near tile: d = (dh_j + eh) + (dl_j + el), el per target in registers here.
+template <class Sh, bool MASK>
+__device__ __forceinline__ void tile_near(const float4* __restrict__ tile, int ngroups,
+                                          int64_t slot0, Target (&tg)[Sh::IPT],
+                                          const f2 (&el)[Sh::IPT][3], f2 eps2) {
+#pragma unroll 1
+  for (int g = 0; g < ngroups; ++g) {
+    const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
+    const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
+                     vy = G[cVY], vz = G[cVZ], dxl = G[cDXL], dyl = G[cDYL], dzl = G[cDZL];
+    const int64_t js = slot0 + 4 * g;
+#pragma unroll
+    for (int r = 0; r < Sh::IPT; ++r) {
+      Target& s = tg[r];
+      pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.x, s.ex), f2_add(dxl.x, el[r][0])),
+                          f2_add(f2_add(dyh.x, s.ey), f2_add(dyl.x, el[r][1])),
+                          f2_add(f2_add(dzh.x, s.ez), f2_add(dzl.x, el[r][2])),
+                          f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
+                          eps2, js);
+      pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.y, s.ex), f2_add(dxl.y, el[r][0])),
+                          f2_add(f2_add(dyh.y, s.ey), f2_add(dyl.y, el[r][1])),
+                          f2_add(f2_add(dzh.y, s.ez), f2_add(dzl.y, el[r][2])),
+                          f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
+                          eps2, js + 2);
+    }
+  }
+}
+
+__device__ __forceinline__ float lanes_sum(f2& v) {
+  const float2 p = f2_unpack(v);
+  v = 0ull;
+  return p.x + p.y;
+}
+
+// Compensated totals of one target: 10 (hi, lo) pairs, in registers or in
+// shared memory (one column per thread).
+template <bool SMT, int NT>
+struct Totals {
+  float h[10], l[10];
+  __device__ __forceinline__ void zero(float*) {
+#pragma unroll
+    for (int c = 0; c < 10; ++c) h[c] = l[c] = 0.f;
+  }
+  __device__ __forceinline__ void add(float*, int c, float x) { two_sum_acc(h[c], l[c], x); }
+  __device__ __forceinline__ double get(float*, int c) const { return (double)h[c] + (double)l[c]; }
+};
+template <int NT>
+struct Totals<true, NT> {
+  // column of this thread: col[(2 c) NT] = hi, col[(2 c + 1) NT] = lo
+  __device__ __forceinline__ void zero(float* col) {
+#pragma unroll
+    for (int c = 0; c < 20; ++c) col[c * NT] = 0.f;
+  }
+  __device__ __forceinline__ void add(float* col, int c, float x) {
+    float hi = col[(2 * c) * NT], lo = col[(2 * c + 1) * NT];
+    two_sum_acc(hi, lo, x);
+    col[(2 * c) * NT] = hi;
+    col[(2 * c + 1) * NT] = lo;
+  }
+  __device__ __forceinline__ double get(float* col, int c) const {
+    return (double)col[(2 * c) * NT] + (double)col[(2 * c + 1) * NT];
+  }
+};
+
+template <class Sh>
+__device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT>& T, float* col) {
+  T.add(col, 0, lanes_sum(s.ax));
+  T.add(col, 1, lanes_sum(s.ay));
+  T.add(col, 2, lanes_sum(s.az));
+  T.add(col, 3, lanes_sum(s.j1x));
+  T.add(col, 4, lanes_sum(s.j1y));
+  T.add(col, 5, lanes_sum(s.j1z));
+  T.add(col, 6, lanes_sum(s.j2x));
+  T.add(col, 7, lanes_sum(s.j2y));
+  T.add(col, 8, lanes_sum(s.j2z));
+  if (Sh::POT) T.add(col, 9, lanes_sum(s.pt));
+}
+
+// Tile t0 .. t0 + cnt of the source slots (cnt a multiple of 4) plus its
+// (centre, radius) record.
+__device__ __forceinline__ void issue_tile(float4* stage, float4* rec, uint64_t* bar,
+                                           const float4* src, const float4* tiles,
+                                           int64_t t0, int64_t cnt, int64_t tile_idx) {
+  const uint32_t bytes = static_cast<uint32_t>(cnt / 4) * kGroupBytes;
+  mbar_arrive_expect(bar, bytes + 32u);
+  bulk_g2s(stage, src + (t0 >> 2) * kGroupF4, bytes, bar);
+  bulk_g2s(rec, tiles + 2 * tile_idx, 32u, bar);
+}
+
+template <class Sh>
+__global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArgs a) {
+  constexpr int NT = Sh::NT, IPT = Sh::IPT, NI = Sh::NI;
+  __shared__ __align__(128) float4 stage[2][kTileF4];
+  __shared__ __align__(16) float4 rec[2][2];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int abort_flag;
+  __shared__ float tot_sh[Sh::SMT ? IPT * 20 * NT : 1];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  uint32_t used[2] = {0u, 0u};  // completed phases per stage
+  bool pending[2] = {false, false};
+  const float4* __restrict__ src = static_cast<const float4*>(a.src_a);
+  const float4* __restrict__ tiles = a.tiles;
+  const float e2 = static_cast<float>(a.eps2);
+  const f2 eps2 = f2_pack(e2, e2);
+  const int32_t n_items = a.item_off[a.K];
+
+  for (int32_t w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int32_t k = upper_bound_i32(a.item_off, a.K + 1, w) - 1;
+    const int32_t B = a.bfac[k];
+    const int32_t l = w - a.item_off[k];
+    const int32_t it = l / B;
+    const int32_t b = l - it * B;
+    const int64_t sk0 = a.soff[k];
+    const int64_t S_k = a.soff[k + 1] - sk0;
+    const int64_t L = chunk_len(S_k, B, JT);
+    const int64_t j0 = sk0 + b * L;
+    const int64_t j1 = sk0 + min(S_k, (int64_t)(b + 1) * L);
+    const int64_t tk0 = a.toff[k];
+    const int32_t a0 = a.act_off[k];
+    const int32_t m_k = a.act_off[k + 1] - a0;
+    const int64_t p0 = a.off[k], p1 = a.off[k + 1];
+
+    Target tg[IPT];
+    Totals<Sh::SMT, NT> tot[IPT];
+    bool valid[IPT];
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) {
+      const int32_t q = it * NI + r * NT + tid;
+      valid[r] = q < m_k;
+      float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f, vx = 0.f, vy = 0.f,
+            vz = 0.f;
+      tg[r].slot = -1;
+      if (valid[r]) {
+        const int32_t s = a0 + q;
+        const int64_t p = a.active ? (int64_t)a.active[s] : (int64_t)s;
+        if (p < p0 || p >= p1) {
+          valid[r] = false;
+          atomicOr(a.status, kStatusInval);
+        } else {
+          const int64_t slot = a.sinv ? (int64_t)a.sinv[p] : sk0 + (p - p0);
+          const float* gp =
+              reinterpret_cast<const float*>(src + (slot >> 2) * kGroupF4) + (slot & 3);
+          // absolute position = own tile centre + offset, in double-single
+          const float4* tr = tiles + 2 * (tk0 + (slot - sk0) / JT);
+          const float4 ch = tr[0], cl = tr[1];
+          ds_sub(ch.x, cl.x, -gp[4 * cDXH], -gp[4 * cDXL], xh, xl);
+          ds_sub(ch.y, cl.y, -gp[4 * cDYH], -gp[4 * cDYL], yh, yl);
+          ds_sub(ch.z, cl.z, -gp[4 * cDZH], -gp[4 * cDZL], zh, zl);
+          vx = gp[4 * cVX];
+          vy = gp[4 * cVY];
+          vz = gp[4 * cVZ];
+          tg[r].slot = slot;
+        }
+      }
+      tg[r].xh = xh; tg[r].yh = yh; tg[r].zh = zh;
+      tg[r].xl = xl; tg[r].yl = yl; tg[r].zl = zl;
+      tg[r].nvx = bcast(-vx); tg[r].nvy = bcast(-vy); tg[r].nvz = bcast(-vz);
+      tg[r].ax = tg[r].ay = tg[r].az = 0ull;
+      tg[r].j1x = tg[r].j1y = tg[r].j1z = 0ull;
+      tg[r].j2x = tg[r].j2y = tg[r].j2z = 0ull;
+      tg[r].pt = 0ull;
+      tot[r].zero(tot_sh + r * 20 * NT + tid);
+    }
+
+    const int64_t ntile = ceil_div64(j1 - j0, JT);
+    if (tid == 0) {
+      issue_tile(stage[0], rec[0], &bar[0], src, tiles, j0, min((int64_t)JT, j1 - j0),
+                 tk0 + (j0 - sk0) / JT);
+      pending[0] = true;
+      if (ntile > 1) {
+        issue_tile(stage[1], rec[1], &bar[1], src, tiles, j0 + JT,
+                   min((int64_t)JT, j1 - j0 - JT), tk0 + (j0 - sk0) / JT + 1);
+        pending[1] = true;
+      }
+    }
+    for (int64_t t = 0; t < ntile; ++t) {
+      const int st = static_cast<int>(t & 1);
+      const int64_t t0 = j0 + t * JT;
+      const int64_t cnt = min((int64_t)JT, j1 - t0);
+      const bool ok = mbar_wait(&bar[st], used[st] & 1u, kWaitBudget);
+      used[st] += 1;
+      if (tid == 0) pending[st] = false;
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(a.status, kStatusTimeout);
+      }
+      // every thread of the CTA reaches the vote below (ok is CTA-uniform in
+      // practice; a thread whose wait failed votes "near" and skips the work)
+      const float4 ch = rec[st][0], cl = rec[st][1];
+      const float far_lim = kFarRatio2 * ch.w * ch.w;
+      bool far = ok;
+      bool self = false;
+#pragma unroll
+      for (int r = 0; r < IPT; ++r) {
+        float exh, exl, eyh, eyl, ezh, ezl;
+        ds_sub(ch.x, cl.x, tg[r].xh, tg[r].xl, exh, exl);
+        ds_sub(ch.y, cl.y, tg[r].yh, tg[r].yl, eyh, eyl);
+        ds_sub(ch.z, cl.z, tg[r].zh, tg[r].zl, ezh, ezl);
+        tg[r].ex = bcast(exh);
+        tg[r].ey = bcast(eyh);
+        tg[r].ez = bcast(ezh);
+        const float d2 = exh * exh + eyh * eyh + ezh * ezh;
+        far = far && (!valid[r] || d2 > far_lim);
+        self |= (tg[r].slot >= t0) && (tg[r].slot < t0 + cnt);
+      }
+      const bool warp_far = __all_sync(0xffffffffu, far);
+      if (ok) {
+        const int ng = static_cast<int>(cnt >> 2);
+        if (warp_far) {
+          tile_far<Sh>(stage[st], ng, tg, eps2);
+        } else {
+          f2 el[IPT][3];
+#pragma unroll
+          for (int r = 0; r < IPT; ++r) {
+            float h, lo;
+            ds_sub(ch.x, cl.x, tg[r].xh, tg[r].xl, h, lo);
+            el[r][0] = bcast(lo);
+            ds_sub(ch.y, cl.y, tg[r].yh, tg[r].yl, h, lo);
+            el[r][1] = bcast(lo);
+            ds_sub(ch.z, cl.z, tg[r].zh, tg[r].zl, h, lo);
+            el[r][2] = bcast(lo);
+          }
+          if (self)
+            tile_near<Sh, true>(stage[st], ng, t0, tg, el, eps2);
+          else
+            tile_near<Sh, false>(stage[st], ng, t0, tg, el, eps2);
+        }
+#pragma unroll
+        for (int r = 0; r < IPT; ++r) flush<Sh>(tg[r], tot[r], tot_sh + r * 20 * NT + tid);
+      }
+      __syncthreads();
+      if (abort_flag) goto drain;
+      if (tid == 0 && t + 2 < ntile) {
+        issue_tile(stage[st], rec[st], &bar[st], src, tiles, t0 + 2 * JT,
+                   min((int64_t)JT, j1 - t0 - 2 * JT), tk0 + (t0 - sk0) / JT + 2);
+        pending[st] = true;
+      }
+    }
+
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) {
+      if (!valid[r]) continue;
+      float* col = tot_sh + r * 20 * NT + tid;
+      double v[kPartialComps];
+      v[0] = tot[r].get(col, 0);
+      v[1] = tot[r].get(col, 1);
+      v[2] = tot[r].get(col, 2);
+      v[3] = tot[r].get(col, 3) - 3.0 * tot[r].get(col, 6);
+      v[4] = tot[r].get(col, 4) - 3.0 * tot[r].get(col, 7);
+      v[5] = tot[r].get(col, 5) - 3.0 * tot[r].get(col, 8);
+      v[6] = Sh::POT ? -tot[r].get(col, 9) : 0.0;
+      const int32_t ql = r * NT + tid;
+      if (B == 1) {
+        const int64_t srow = a0 + it * NI + ql;
+        if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[srow * a.sa + c] = a.G * v[c];
+        if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[srow * a.sj + c] = a.G * v[3 + c];
+        if (Sh::POT && a.out_pot) a.out_pot[srow * a.sp] = a.G * v[6];
+      } else {
+        double* P = a.partials + (size_t)w * kPartialComps * NI + ql;
+#pragma unroll
+        for (int c = 0; c < kPartialComps; ++c) P[(size_t)c * NI] = v[c];
+      }
+    }
+  }
+  return;
+
+drain:
+  // A wait gave up: let any copy still in flight land (bounded) before the
+  // CTA's shared memory is released.
+  if (tid == 0) {
+    for (int st = 0; st < 2; ++st)
+      if (pending[st]) (void)mbar_wait(&bar[st], used[st] & 1u, kWaitBudget);
+  }
+}
+
+}  // namespace mixk
+}  // namespace nb

@@ -38,26 +38,6 @@ __device__ __forceinline__ void predict1(const dbl4& p, const dbl4& v, const dbl
   vp.z = v.z + t * (a.z + h * j.z);
 }
 
-__device__ __forceinline__ float hi_part(double x) { return __double2float_rn(x); }
-
-// Mixed source slot: component c of slot s lives at float index
-// ((s >> 2) * 10 + c) * 4 + (s & 3).
-__device__ __forceinline__ void write_mixed(float4* src, int64_t slot, const double3& x,
-                                            double m, const double3& v) {
-  float* g = reinterpret_cast<float*>(src + (slot >> 2) * 10) + (slot & 3);
-  const float xh = hi_part(x.x), yh = hi_part(x.y), zh = hi_part(x.z);
-  g[0] = xh;
-  g[4] = yh;
-  g[8] = zh;
-  g[12] = static_cast<float>(m);
-  g[16] = __double2float_rn(x.x - (double)xh);
-  g[20] = __double2float_rn(x.y - (double)yh);
-  g[24] = __double2float_rn(x.z - (double)zh);
-  g[28] = __double2float_rn(v.x);
-  g[32] = __double2float_rn(v.y);
-  g[36] = __double2float_rn(v.z);
-}
-
 template <typename T, typename Op>
 __device__ __forceinline__ T block_reduce(T v, Op op, T* sh, T ident) {
   // blockDim.x a multiple of 32, <= 1024
@@ -114,21 +94,6 @@ __global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
     p[i] = v;
 }
 
-// Massless pad sources (slots N_k .. round_up(N_k, 4) of each cluster), placed
-// far away so that every term they contribute is exactly zero.
-__global__ void k_init_pads(Dev d) {
-  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < d.K; k += gridDim.x * blockDim.x) {
-    const int64_t nk = d.off[k + 1] - d.off[k];
-    for (int64_t s = d.soff[k] + nk; s < d.soff[k + 1]; ++s) {
-      const double3 x = make_double3(kDummyPos, kDummyPos, kDummyPos);
-      const double3 v = make_double3(0.0, 0.0, 0.0);
-      write_mixed(d.src_mix, s, x, 0.0, v);
-      d.src64_pos[s] = dbl4{kDummyPos, kDummyPos, kDummyPos, 0.0};
-      d.src64_vel[s] = dbl4{0.0, 0.0, 0.0, 0.0};
-    }
-  }
-}
-
 // Next block time of every cluster whose time is below the end time.
 __global__ void k_tmin(Dev d, int T) {
   __shared__ long long sh[32];
@@ -154,42 +119,6 @@ __global__ void k_tmin(Dev d, int T) {
   }
 }
 
-// Predict every particle to the target time of its cluster (t_tgt[c], or
-// t_fixed when t_tgt is null; clusters whose target is LLONG_MAX are left
-// alone) and write the source arrays.  With count_due, also count the
-// particles due at the target time per block of kScanBlock particles.
-__global__ void k_predict(Dev d, const int64_t* t_tgt, int64_t t_fixed, int T, int write_mix,
-                          int write64, int count_due) {
-  __shared__ int32_t sh[32];
-  const int64_t base = blockIdx.x * (int64_t)kScanBlock;
-  int32_t cnt = 0;
-#pragma unroll
-  for (int q = 0; q < kScanBlock / kScanThreads; ++q) {
-    const int64_t i = base + q * kScanThreads + threadIdx.x;
-    if (i >= d.N) break;
-    const int32_t c = d.cid[i];
-    const int64_t tn = t_tgt ? t_tgt[c] : t_fixed;
-    if (tn == LLONG_MAX) continue;
-    const int64_t ti = d.t[i];
-    if (count_due && ti + step_ticks(d.level[i], T) == tn) ++cnt;
-    const double tau = ldexp((double)(tn - ti), -T);
-    const dbl4 p = d.pos[i], v = d.vel[i], a = d.acc[i], j = d.jerk[i];
-    double3 xp, vp;
-    predict1(p, v, a, j, tau, xp, vp);
-    const int64_t slot = d.soff[c] + (i - d.off[c]);
-    if (write_mix) write_mixed(d.src_mix, slot, xp, p.w, vp);
-    if (write64) {
-      d.src64_pos[slot] = dbl4{xp.x, xp.y, xp.z, p.w};
-      d.src64_vel[slot] = dbl4{vp.x, vp.y, vp.z, 0.0};
-    }
-  }
-  if (count_due) {
-    const int32_t tot =
-        block_reduce<int32_t>(cnt, [](int32_t x, int32_t y) { return x + y; }, sh, 0);
-    if (threadIdx.x == 0) d.blk_count[blockIdx.x] = tot;
-  }
-}
-
 // Exclusive scan of nblk block counts (one CTA of 1024 threads); the total
 // goes to act_off[K].
 __global__ void k_scan(Dev d, int32_t nblk) {
@@ -206,28 +135,72 @@ __global__ void k_scan(Dev d, int32_t nblk) {
   if (threadIdx.x == 0) d.act_off[d.K] = carry;
 }
 
-// Active list in ascending particle order, plus each cluster's offset in it.
-__global__ void k_scatter(Dev d, int T) {
-  __shared__ int32_t sh[32];
-  const int64_t base = blockIdx.x * (int64_t)kScanBlock;
-  int32_t run = d.blk_count[blockIdx.x];
-#pragma unroll
-  for (int q = 0; q < kScanBlock / kScanThreads; ++q) {
-    const int64_t i = base + q * kScanThreads + threadIdx.x;
-    int32_t f = 0, c = -1;
-    if (i < d.N) {
-      c = d.cid[i];
-      const int64_t tn = d.t_min[c];
-      f = (tn != LLONG_MAX && d.t[i] + step_ticks(d.level[i], T) == tn) ? 1 : 0;
-    }
-    int32_t tot;
-    const int32_t ex = block_excl_scan(f, sh, &tot);
-    if (i < d.N) {
-      if (f) d.active[run + ex] = static_cast<int32_t>(i);
-      if (i == d.off[c]) d.act_off[c] = run + ex;
-    }
-    run += tot;
+// Predict the particles of one source tile (one CTA of kMixJT threads, one
+// slot per thread) to the target time of their cluster (t_tgt[k], or t_fixed
+// when t_tgt is null; a cluster whose target is LLONG_MAX is skipped) and
+// write them in the force kernels' layouts: FP64 sources, and/or the mixed
+// tile (centre, radius, double-single offsets).  With count_due, also count
+// the tile's particles due at the target time.
+__global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* t_tgt,
+                                                          int64_t t_fixed, int T, int write_mix,
+                                                          int write64, int count_due) {
+  __shared__ double shd[32];
+  __shared__ int32_t shi[32];
+  const int32_t tile = blockIdx.x;
+  const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
+  const int64_t s = d.soff[k] + (int64_t)(tile - d.toff[k]) * kMixJT + threadIdx.x;
+  const bool in = s < d.soff[k + 1];
+  const int32_t p = in ? d.sperm[s] : -1;
+  const int64_t tn = t_tgt ? t_tgt[k] : t_fixed;
+  if (tn == LLONG_MAX) {  // uniform over the CTA: the whole tile is one cluster
+    if (count_due && threadIdx.x == 0) d.blk_count[tile] = 0;
+    return;
   }
+  int32_t due = 0;
+  double3 xp = make_double3(0.0, 0.0, 0.0), vp = make_double3(0.0, 0.0, 0.0);
+  double m = 0.0;
+  if (p >= 0) {
+    const int64_t ti = d.t[p];
+    due = (count_due && ti + step_ticks(d.level[p], T) == tn) ? 1 : 0;
+    const double tau = ldexp((double)(tn - ti), -T);
+    const dbl4 P = d.pos[p], V = d.vel[p], A = d.acc[p], J = d.jerk[p];
+    predict1(P, V, A, J, tau, xp, vp);
+    m = P.w;
+  }
+  if (count_due) {
+    const int32_t tot =
+        block_reduce<int32_t>(due, [](int32_t x, int32_t y) { return x + y; }, shi, 0);
+    if (threadIdx.x == 0) d.blk_count[tile] = tot;
+  }
+  if (write64 && in) {
+    if (p >= 0) {
+      d.src64_pos[s] = dbl4{xp.x, xp.y, xp.z, m};
+      d.src64_vel[s] = dbl4{vp.x, vp.y, vp.z, 0.0};
+    } else {
+      d.src64_pos[s] = dbl4{kDummyPos, kDummyPos, kDummyPos, 0.0};
+      d.src64_vel[s] = dbl4{0.0, 0.0, 0.0, 0.0};
+    }
+  }
+  if (write_mix) build_mixed_tile(d.src_mix, d.tiles, tile, s, in, p >= 0, xp, m, vp, shd);
+}
+
+// Active list in source-slot order (spatially sorted targets), plus each
+// cluster's offset in it; one CTA per source tile as in k_predict_tiles.
+__global__ void __launch_bounds__(kMixJT) k_scatter_tiles(Dev d, int T) {
+  __shared__ int32_t sh[32];
+  const int32_t tile = blockIdx.x;
+  const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
+  const int64_t s = d.soff[k] + (int64_t)(tile - d.toff[k]) * kMixJT + threadIdx.x;
+  const bool in = s < d.soff[k + 1];
+  const int32_t p = in ? d.sperm[s] : -1;
+  const int64_t tn = d.t_min[k];
+  const int32_t f =
+      (p >= 0 && tn != LLONG_MAX && d.t[p] + step_ticks(d.level[p], T) == tn) ? 1 : 0;
+  int32_t tot;
+  const int32_t ex = block_excl_scan(f, sh, &tot);
+  const int32_t run = d.blk_count[tile];
+  if (f) d.active[run + ex] = p;
+  if (s == d.soff[k]) d.act_off[k] = run;
 }
 
 // Work plan: per-cluster active count m_k, i-split factor B_k (Sec. 2 item 3)
@@ -465,9 +438,7 @@ __global__ void k_energy_partial(Dev d, const double* pot, int sp, int64_t lo, i
   double ek = 0.0, ep = 0.0;
   for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c = d.cid[i];
-    const int64_t slot = d.soff[c] + (i - d.off[c]);
-    const dbl4 v = d.src64_vel[slot];
+    const dbl4 v = d.src64_vel[d.sinv[i]];
     const double m = d.pos[i].w;
     ek += 0.5 * m * (v.x * v.x + v.y * v.y + v.z * v.z);
     ep += 0.5 * m * pot[i * sp];
@@ -532,23 +503,19 @@ cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t st) {
   k_fill_i64<<<blocks_for(n, 256), 256, 0, st>>>(p, n, v);
   return cudaGetLastError();
 }
-cudaError_t launch_init_pads(const Dev& d, cudaStream_t st) {
-  k_init_pads<<<blocks_for(d.K, 128), 128, 0, st>>>(d);
-  return cudaGetLastError();
-}
 cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st) {
   k_tmin<<<static_cast<int>(ceil_div64(d.N, 256)), 256, 0, st>>>(d, T);
   return cudaGetLastError();
 }
-int scan_blocks(int64_t N) { return static_cast<int>(ceil_div64(N, kScanBlock)); }
 cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T,
                            bool mix, bool f64, bool count_due, cudaStream_t st) {
-  k_predict<<<scan_blocks(d.N), kScanThreads, 0, st>>>(d, t_tgt, t_fixed, T, mix, f64, count_due);
+  k_predict_tiles<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d, t_tgt, t_fixed, T, mix,
+                                                                  f64, count_due);
   return cudaGetLastError();
 }
 cudaError_t launch_compact(const Dev& d, int T, cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(d, scan_blocks(d.N));
-  k_scatter<<<scan_blocks(d.N), kScanThreads, 0, st>>>(d, T);
+  k_scan<<<1, 1024, 0, st>>>(d, static_cast<int32_t>(d.n_tiles));
+  k_scatter_tiles<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d, T);
   return cudaGetLastError();
 }
 cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {

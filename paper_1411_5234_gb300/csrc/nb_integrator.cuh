@@ -1,8 +1,88 @@
 // nb_integrator.cuh -- launch interface of the block-step kernels.
 #pragma once
+#include <math_constants.h>
+
 #include "nb_internal.cuh"
 
 namespace nb {
+
+// Write one mixed source tile (one CTA of kMixJT threads, one slot each):
+// centre c = midpoint of the valid particles' bounding box, rounded to a
+// double-single pair (ch, cl); radius h = max |r_j - c| (rounded up); each
+// valid slot stores its double-single offset r_j - c, mass and FP32
+// velocity; pad slots (in == true, valid == false) hold massless dummies far
+// away.  `sh` is 32 doubles of shared scratch.  Every thread must call this.
+__device__ __forceinline__ double nb_block_reduce_d(double v, bool is_max, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_down_sync(0xffffffffu, v, o);
+    v = is_max ? fmax(v, u) : fmin(v, u);
+  }
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? sh[lane] : (is_max ? -CUDART_INF : CUDART_INF);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_down_sync(0xffffffffu, v, o);
+      v = is_max ? fmax(v, u) : fmin(v, u);
+    }
+    if (lane == 0) sh[0] = v;
+  }
+  __syncthreads();
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void build_mixed_tile(float4* src, float4* tiles, int64_t tile,
+                                                 int64_t s, bool in, bool valid, double3 x,
+                                                 double m, double3 v, double* sh) {
+  const double inf = CUDART_INF;
+  const double lx = nb_block_reduce_d(valid ? x.x : inf, false, sh);
+  const double ly = nb_block_reduce_d(valid ? x.y : inf, false, sh);
+  const double lz = nb_block_reduce_d(valid ? x.z : inf, false, sh);
+  const double hx = nb_block_reduce_d(valid ? x.x : -inf, true, sh);
+  const double hy = nb_block_reduce_d(valid ? x.y : -inf, true, sh);
+  const double hz = nb_block_reduce_d(valid ? x.z : -inf, true, sh);
+  const bool any = lx <= hx;
+  const double cx = any ? 0.5 * (lx + hx) : 0.0, cy = any ? 0.5 * (ly + hy) : 0.0,
+               cz = any ? 0.5 * (lz + hz) : 0.0;
+  const float chx = __double2float_rn(cx), chy = __double2float_rn(cy), chz = __double2float_rn(cz);
+  const float clx = __double2float_rn(cx - (double)chx), cly = __double2float_rn(cy - (double)chy),
+              clz = __double2float_rn(cz - (double)chz);
+  const double ux = (double)chx + (double)clx, uy = (double)chy + (double)cly,
+               uz = (double)chz + (double)clz;  // the centre as represented
+  const double dx = x.x - ux, dy = x.y - uy, dz = x.z - uz;
+  const double r = valid ? sqrt(dx * dx + dy * dy + dz * dz) : 0.0;
+  const double h = nb_block_reduce_d(r, true, sh);
+  if (in) {
+    float* g = reinterpret_cast<float*>(src + (s >> 2) * 10) + (s & 3);
+    if (valid) {
+      const float dxh = __double2float_rn(dx), dyh = __double2float_rn(dy),
+                  dzh = __double2float_rn(dz);
+      g[0] = dxh;
+      g[4] = dyh;
+      g[8] = dzh;
+      g[12] = __double2float_rn(m);
+      g[16] = __double2float_rn(v.x);
+      g[20] = __double2float_rn(v.y);
+      g[24] = __double2float_rn(v.z);
+      g[28] = __double2float_rn(dx - (double)dxh);
+      g[32] = __double2float_rn(dy - (double)dyh);
+      g[36] = __double2float_rn(dz - (double)dzh);
+    } else {
+      g[0] = g[4] = g[8] = static_cast<float>(kDummyPos);
+      g[12] = 0.f;
+      g[16] = g[20] = g[24] = 0.f;
+      g[28] = g[32] = g[36] = 0.f;
+    }
+  }
+  if (threadIdx.x == 0) {
+    tiles[2 * tile] = make_float4(chx, chy, chz, __double2float_ru(h));
+    tiles[2 * tile + 1] = make_float4(clx, cly, clz, 0.f);
+  }
+}
 
 struct PlanArgs {
   int NI;               // targets per work item of the force kernel
@@ -28,9 +108,7 @@ struct CorrectArgs {
 };
 
 cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t st);
-cudaError_t launch_init_pads(const Dev& d, cudaStream_t st);
 cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st);
-int scan_blocks(int64_t N);
 cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T, bool mix,
                            bool f64, bool count_due, cudaStream_t st);
 cudaError_t launch_compact(const Dev& d, int T, cudaStream_t st);

@@ -27,8 +27,6 @@ typedef double4_32a dbl4;
 namespace nb {
 
 constexpr int kMaxTickExp = 60;
-constexpr int kScanBlock = 1024;     // particles per block in predict/scatter
-constexpr int kScanThreads = 256;
 constexpr int kPartialComps = 7;     // ax ay az jx jy jz pot
 constexpr double kDummyPos = 1.0e18; // where massless pad sources sit
 
@@ -57,11 +55,16 @@ struct Dev {
   int32_t* active = nullptr;
   dbl4 *acc_new = nullptr, *jerk_new = nullptr;
   float4* src_mix = nullptr;     // (S / 4) * 10 float4
+  float4* tiles = nullptr;       // 2 float4 per mixed source tile: (c_hi, h), (c_lo, 0)
+  int32_t* toff = nullptr;       // K + 1: first tile of each cluster
+  int64_t n_tiles = 0;
+  int32_t* sperm = nullptr;      // S: particle of each source slot (-1: pad)
+  int32_t* sinv = nullptr;       // N: source slot of each particle
   dbl4* src64_pos = nullptr;  // S
   dbl4* src64_vel = nullptr;  // S
   double* partials = nullptr;    // part_items * 7 * NI_max
   int64_t part_items = 0;
-  int32_t* blk_count = nullptr;  // ceil(N / kScanBlock) + 1
+  int32_t* blk_count = nullptr;  // n_tiles + 1 (due particles per source tile)
   int64_t *off = nullptr, *soff = nullptr;   // K + 1
   int64_t *t_cur = nullptr, *t_min = nullptr; // K
   int32_t *act_off = nullptr, *item_off = nullptr; // K + 1
@@ -80,6 +83,9 @@ struct ForceArgs {
   const int32_t* act_off;   // target offsets per cluster (K + 1)
   const int32_t* item_off;  // work-item offsets per cluster (K + 1)
   const int32_t* bfac;      // i-split factor per cluster (K)
+  const int32_t* sinv;      // source slot of each particle (nullptr: slot order = particle order)
+  const float4* tiles;      // mixed source tile records
+  const int32_t* toff;      // first tile of each cluster (K + 1)
   int32_t K;
   const void* src_a;        // mixed: float4 groups; FP64: positions
   const void* src_b;        // FP64: velocities
@@ -216,9 +222,11 @@ __host__ __device__ __forceinline__ int64_t chunk_len(int64_t S_k, int64_t B, in
 
 // ------------------------------------------------------- launch wrappers
 // (defined in the .cu files; all enqueue on `st` and return the launch error)
-cudaError_t launch_force_mixed(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st);
+cudaError_t launch_force_mixed(const ForceArgs& a, int grid, bool with_pot, int variant,
+                               cudaStream_t st);
 cudaError_t launch_force_fp64(const ForceArgs& a, int grid, int mode, cudaStream_t st);
-int force_mixed_ctas_per_sm();
+int force_mixed_variants();
+int force_mixed_ctas_per_sm(int variant);
 int force_fp64_ctas_per_sm();
 size_t force_mixed_smem();
 size_t force_fp64_smem();

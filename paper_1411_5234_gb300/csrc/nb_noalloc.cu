@@ -11,7 +11,7 @@
 // device array compiled into the library.
 //
 // Properties a caller must know:
-//   * the array is kNoAllocBytes bytes, lives on every GPU that loads the
+//   * the array is kNoAllocBytes (6,697,472) bytes, lives on every GPU that loads the
 //     library, and is held until the process exits;
 //   * at most NB_NOALLOC_MAX_SOURCES sources per call; larger calls are
 //     rejected with NB_EINVAL before anything is launched;
@@ -43,10 +43,13 @@ constexpr size_t kOffSources = 0;  // mixed float4 groups or FP64 pos+vel (the l
 constexpr size_t kSourceBytes = align_up(64 * kNoAllocSlots);
 constexpr size_t kOffPartials = kOffSources + kSourceBytes;
 constexpr size_t kPartialBytes = align_up((size_t)kNoAllocItems * kPartialComps * kMixNI * 8);
-constexpr size_t kOffSmall = kOffPartials + kPartialBytes;
+constexpr int64_t kNoAllocTiles = (kNoAllocSlots + kMixJT - 1) / kMixJT;
+constexpr size_t kOffTiles = kOffPartials + kPartialBytes;
+constexpr size_t kTileBytes = align_up(32 * (size_t)kNoAllocTiles);
+constexpr size_t kOffSmall = kOffTiles + kTileBytes;
 constexpr size_t kSmallBytes = 4096;  // offsets, plan words, status, counters
-constexpr size_t kNoAllocBytes = kOffSmall + kSmallBytes;  // 6,689,024 bytes
-static_assert(kNoAllocBytes == 6689024, "documented size of the fixed array");
+constexpr size_t kNoAllocBytes = kOffSmall + kSmallBytes;  // 6,697,472 bytes
+static_assert(kNoAllocBytes == 6697472, "documented size of the fixed array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -60,52 +63,55 @@ struct DeviceSetup {
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-// Sources in the force kernels' layouts, the single-cluster offsets, and the
-// zeroed status word.
-__global__ void k_noalloc_pack(const double* pos, const double* vel, const double* mass,
-                               int64_t n, int64_t n_pad, int64_t m, int mixed, float4* src_mix,
-                               dbl4* src_pos, dbl4* src_vel, int64_t* off, int64_t* soff,
-                               int32_t* act_off, uint32_t* status) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid == 0) {
+// Single-cluster offsets, the identity source order and the zeroed status.
+__global__ void k_noalloc_setup(int64_t n, int64_t n_pad, int64_t m, int32_t n_tiles,
+                                int64_t* off, int64_t* soff, int32_t* act_off, int32_t* toff,
+                                uint32_t* status) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     off[0] = 0;
     off[1] = n;
     soff[0] = 0;
     soff[1] = n_pad;
     act_off[0] = 0;
     act_off[1] = static_cast<int32_t>(m);
+    toff[0] = 0;
+    toff[1] = n_tiles;
     *status = 0u;
   }
-  for (int64_t s = tid; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
-    double x = kDummyPos, y = kDummyPos, z = kDummyPos, w = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
+}
+
+// FP64 sources straight from the caller's arrays (pads: massless, far away).
+__global__ void k_noalloc_pack64(const double* pos, const double* vel, const double* mass,
+                                 int64_t n, int64_t n_pad, dbl4* src_pos, dbl4* src_vel) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad;
+       s += (int64_t)gridDim.x * blockDim.x) {
     if (s < n) {
-      x = pos[3 * s];
-      y = pos[3 * s + 1];
-      z = pos[3 * s + 2];
-      w = mass[s];
-      vx = vel[3 * s];
-      vy = vel[3 * s + 1];
-      vz = vel[3 * s + 2];
-    }
-    if (mixed) {
-      // double-single split: hi = fl32(x), lo = fl32(x - hi)
-      float* g = reinterpret_cast<float*>(src_mix + (s >> 2) * 10) + (s & 3);
-      const float xh = __double2float_rn(x), yh = __double2float_rn(y), zh = __double2float_rn(z);
-      g[0] = xh;
-      g[4] = yh;
-      g[8] = zh;
-      g[12] = __double2float_rn(w);
-      g[16] = __double2float_rn(x - (double)xh);
-      g[20] = __double2float_rn(y - (double)yh);
-      g[24] = __double2float_rn(z - (double)zh);
-      g[28] = __double2float_rn(vx);
-      g[32] = __double2float_rn(vy);
-      g[36] = __double2float_rn(vz);
+      src_pos[s] = dbl4{pos[3 * s], pos[3 * s + 1], pos[3 * s + 2], mass[s]};
+      src_vel[s] = dbl4{vel[3 * s], vel[3 * s + 1], vel[3 * s + 2], 0.0};
     } else {
-      src_pos[s] = dbl4{x, y, z, w};
-      src_vel[s] = dbl4{vx, vy, vz, 0.0};
+      src_pos[s] = dbl4{kDummyPos, kDummyPos, kDummyPos, 0.0};
+      src_vel[s] = dbl4{0.0, 0.0, 0.0, 0.0};
     }
   }
+}
+
+// Mixed source tiles (one CTA of kMixJT threads per tile) from the caller's
+// arrays, in particle order.
+__global__ void __launch_bounds__(kMixJT) k_noalloc_pack_mix(const double* pos, const double* vel,
+                                                             const double* mass, int64_t n,
+                                                             int64_t n_pad, float4* src,
+                                                             float4* tiles) {
+  __shared__ double sh[32];
+  const int64_t s = (int64_t)blockIdx.x * kMixJT + threadIdx.x;
+  const bool in = s < n_pad, valid = s < n;
+  double3 x = make_double3(0.0, 0.0, 0.0), v = make_double3(0.0, 0.0, 0.0);
+  double m = 0.0;
+  if (valid) {
+    x = make_double3(pos[3 * s], pos[3 * s + 1], pos[3 * s + 2]);
+    v = make_double3(vel[3 * s], vel[3 * s + 1], vel[3 * s + 2]);
+    m = mass[s];
+  }
+  build_mixed_tile(src, tiles, blockIdx.x, s, in, valid, x, m, v, sh);
 }
 
 int setup_device(DeviceSetup** out) {
@@ -173,14 +179,21 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   d.src64_vel = reinterpret_cast<dbl4*>(base + kOffSources + 32 * kNoAllocSlots);
   d.partials = reinterpret_cast<double*>(base + kOffPartials);
   d.part_items = kNoAllocItems;
+  d.tiles = reinterpret_cast<float4*>(base + kOffTiles);
+  d.toff = small32 + 16;     // 2 entries
+  const int32_t n_tiles = static_cast<int32_t>((n_pad + kMixJT - 1) / kMixJT);
 
-  int grid_blocks = static_cast<int>((n_pad + 255) / 256);
-  k_noalloc_pack<<<grid_blocks, 256, 0, st>>>(pos, vel, mass, n, n_pad, m, f64 ? 0 : 1,
-                                              d.src_mix, d.src64_pos, d.src64_vel, d.off,
-                                              d.soff, d.act_off, d.status);
+  k_noalloc_setup<<<1, 32, 0, st>>>(n, n_pad, m, n_tiles, d.off, d.soff, d.act_off, d.toff,
+                                    d.status);
+  if (f64)
+    k_noalloc_pack64<<<static_cast<int>((n_pad + 255) / 256), 256, 0, st>>>(
+        pos, vel, mass, n, n_pad, d.src64_pos, d.src64_vel);
+  else
+    k_noalloc_pack_mix<<<n_tiles, kMixJT, 0, st>>>(pos, vel, mass, n, n_pad, d.src_mix,
+                                                   d.tiles);
   if (cudaGetLastError() != cudaSuccess) return NB_ECUDA;
 
-  const int grid = ds->sms * (f64 ? force_fp64_ctas_per_sm() : force_mixed_ctas_per_sm());
+  const int grid = ds->sms * (f64 ? force_fp64_ctas_per_sm() : force_mixed_ctas_per_sm(1));
   PlanArgs p{};
   p.NI = f64 ? kF64NI : kMixNI;
   p.JT = f64 ? kF64JT : kMixJT;
@@ -198,6 +211,9 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   a.act_off = d.act_off;
   a.item_off = d.item_off;
   a.bfac = d.bfac;
+  a.sinv = nullptr;  // sources in particle order
+  a.tiles = d.tiles;
+  a.toff = d.toff;
   a.K = 1;
   a.src_a = f64 ? static_cast<const void*>(d.src64_pos) : static_cast<const void*>(d.src_mix);
   a.src_b = f64 ? d.src64_vel : nullptr;
@@ -212,7 +228,7 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   a.eps2 = eps * eps;
   a.status = d.status;
   cudaError_t e = f64 ? launch_force_fp64(a, grid, kF64Full, st)
-                      : launch_force_mixed(a, grid, pot != nullptr, st);
+                      : launch_force_mixed(a, grid, pot != nullptr, 1, st);
   if (e != cudaSuccess) return NB_ECUDA;
   if (launch_reduce(a, p.NI, true, m, st) != cudaSuccess) return NB_ECUDA;
   return NB_OK;

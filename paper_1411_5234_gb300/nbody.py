@@ -32,7 +32,8 @@ class NbConfig(ctypes.Structure):
                 ("eta_start", ctypes.c_double), ("level_min", ctypes.c_int32),
                 ("level_max", ctypes.c_int32), ("tick_exp", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("bfactor", ctypes.c_int32),
-                ("graph_steps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("graph_steps", ctypes.c_int32), ("sort_sources", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
 
 
 class NBError(RuntimeError):
