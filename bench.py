@@ -88,7 +88,9 @@ def kernel_case(args):
     assert sim.status() == nbody.NB_OK
     per = ms / max(cnt, 1)
     rate = args.m * cl.n / (per * 1e-3)
+    wt, nt = sim.tile_stats()
     print(json.dumps({"kernel_case": args.kernel_case, "variant": sim.cfg.variant,
+                      "near_tile_share": nt / max(wt, 1),
                       "N": cl.n, "m": args.m,
                       "ms_per_launch": per, "interactions_per_s": rate,
                       "frac_fp32_peak_38": FLOPS_PER_INTERACTION * rate
@@ -267,8 +269,9 @@ def main():
     n = args.n
     cl = make_cluster(n, seed=rank)
     L = args.level
+    kw = {} if args.variant is None else {"variant": args.variant}
     sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nbody.NB_MIXED,
-                    level_min=L, level_max=L, graph_steps=0)
+                    level_min=L, level_max=L, graph_steps=0, **kw)
     stream = sim.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     sim.profile(True)
@@ -331,6 +334,9 @@ def main():
         roofline["peak_at_sampled_clock"] = pk
         roofline["frac_at_sampled_clock"] = achieved / pk
 
+    roofline["kernel_shape_variant"] = sim.cfg.variant
+    wt, nt = sim.tile_stats()
+    roofline["near_tile_share"] = nt / max(wt, 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

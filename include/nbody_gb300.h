@@ -87,7 +87,7 @@ typedef struct {
     int32_t precision;  /* nb_precision                                        */
     int32_t bfactor;    /* i-split factor B: 0 = chosen per step by the plan   */
     int32_t graph_steps;/* block steps captured per CUDA graph (0 = no graph)  */
-    int32_t sort_sources;/* 1: force sources kept in spatial (Morton) order of
+    int32_t sort_sources;/* 1: force sources kept in spatial (Hilbert) order of
                             the initial positions, 0: in particle order.  Only
                             speed depends on it, never the results' accuracy. */
     int32_t variant;    /* shape of the mixed force kernel, 0..3 (see
@@ -97,7 +97,7 @@ typedef struct {
 
 /* Defaults: G = 1, eps = 1e-4, eta = 0.01, eta_start = 0.01, level_min = 0,
  * level_max = 30, tick_exp = 40, NB_MIXED, bfactor = 0, graph_steps = 16,
- * sort_sources = 1, variant = 1. */
+ * sort_sources = 1, variant = 2. */
 void nb_default_config(nb_config *cfg);
 
 /* Bytes of the device workspace for n_total particles in n_clusters clusters
@@ -128,13 +128,14 @@ void nb_free(nb_ctx *ctx);
 int nb_predict(nb_ctx *ctx, int64_t t_ticks);
 
 /* Acceleration, jerk and potential (Eq. 1, Eq. 2) of the m particles listed in
- * active_idx (device int32, m entries, global particle indices, strictly
- * ascending) from the predicted sources of their own cluster (the last
+ * active_idx (device int32, m entries, global particle indices in any order,
+ * no repeats) from the predicted sources of their own cluster (the last
  * nb_predict).  acc and jerk: device (m x 3) doubles; pot: device m doubles
- * or NULL.  Row k of the outputs belongs to active_idx[k].  m == 0 is a
- * no-op.  Asynchronous; an unsorted or out-of-range list sets the sticky
- * status to NB_EINVAL and the rows of the offending entries are left
- * unwritten. */
+ * or NULL.  Row k of the outputs belongs to active_idx[k].  The targets are
+ * evaluated in the library's spatial source order and written back to their
+ * rows.  m == 0 is a no-op.  Asynchronous; an out-of-range or repeated entry
+ * sets the sticky status to NB_EINVAL and the rows of the offending entries
+ * are left unwritten. */
 int nb_force(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
              double *jerk, double *pot);
 
@@ -193,6 +194,13 @@ int nb_stats(nb_ctx *ctx, int64_t *block_steps, int64_t *interactions,
 int nb_profile_enable(nb_ctx *ctx, int enable);
 int nb_profile_read(nb_ctx *ctx, double *force_ms, int64_t *launches);
 
+/* Mixed force kernel diagnostics since nb_init (host outputs, either may be
+ * NULL): source tiles processed by a warp, and how many of those took the
+ * near (full double-single) path because some target of the warp lay within
+ * 2.5 tile radii.  The near share measures how well the spatial source order
+ * fits the targets; it affects speed only.  Synchronises. */
+int nb_tile_stats(nb_ctx *ctx, int64_t *warp_tiles, int64_t *near_warp_tiles);
+
 /* Sticky device status (NB_OK or an NB_E* code); synchronises. */
 int nb_status(nb_ctx *ctx);
 
@@ -215,7 +223,7 @@ const char *nb_strerror(int code);
  * [0, n) leaves its row unspecified.
  *
  * It allocates nothing: the packed sources, the i-split partial sums and the
- * plan words live in one fixed device array of 6,697,472 bytes compiled into
+ * plan words live in one fixed device array of 6,705,664 bytes compiled into
  * the library, present on every GPU that loads the library until the process
  * exits.  Limits: 1 <= n <= NB_NOALLOC_MAX_SOURCES (larger n returns
  * NB_EINVAL without launching anything), 0 <= m <= n.  All calls on a device

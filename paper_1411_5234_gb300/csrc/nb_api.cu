@@ -23,7 +23,7 @@ constexpr int kEnergyBlocks = 304;
 struct Layout {
   size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
       src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, bfac, esum,
-      status, counters, t_end, tiles, toff, sperm, sinv, total;
+      status, counters, t_end, tiles, toff, sperm, sinv, mark, rows, total;
   int64_t S, part_items, n_tiles;
 };
 
@@ -37,7 +37,7 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
   Layout L{};
   L.S = S;
   L.n_tiles = n_tiles;
-  const int64_t nitile = ceil_div64(N, kF64NI) + K;
+  const int64_t nitile = ceil_div64(N, 128) + K;  // smallest targets-per-item of any shape
   L.part_items = 2 * nitile > 2048 ? 2 * nitile : 2048;
   const size_t ni_max = kMixNI > kF64NI ? kMixNI : kF64NI;
   size_t c = 0;
@@ -67,10 +67,12 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
   L.status = take(c, 4);
   L.counters = take(c, 8 * 4);
   L.t_end = take(c, 8);
-  L.tiles = take(c, 32 * (size_t)n_tiles);
+  L.tiles = take(c, 16 * kTileRecF4 * (size_t)n_tiles);
   L.toff = take(c, 4 * ((size_t)K + 1));
   L.sperm = take(c, 4 * (size_t)S);
   L.sinv = take(c, 4 * (size_t)N);
+  L.mark = take(c, 4 * (size_t)N);
+  L.rows = take(c, 4 * (size_t)N);
   L.total = c;
   return L;
 }
@@ -101,19 +103,40 @@ int64_t tiles_of(const int64_t* off, int32_t K) {
   return n;
 }
 
-// 3-D Morton (Z-order) key of a point quantised to 21 bits per axis.
-uint64_t spread3(uint64_t v) {
-  v &= 0x1fffffull;
-  v = (v | (v << 32)) & 0x1f00000000ffffull;
-  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
-  v = (v | (v << 8)) & 0x100f00f00f00f00full;
-  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
-  v = (v | (v << 2)) & 0x1249249249249249ull;
-  return v;
+// 3-D Hilbert-curve key of a point quantised to `bits` bits per axis (Skilling,
+// "Programming the Hilbert curve", AIP Conf. Proc. 707, 381, 2004): the axes
+// are transformed in place into the transposed Hilbert index, whose bits are
+// then interleaved most significant first.  Consecutive keys are neighbouring
+// cells (no jumps), so fixed-size runs of sorted particles are compact.
+uint64_t hilbert_key(uint32_t x, uint32_t y, uint32_t z, int bits) {
+  uint32_t X[3] = {x, y, z};
+  const uint32_t M = 1u << (bits - 1);
+  for (uint32_t Q = M; Q > 1; Q >>= 1) {
+    const uint32_t P = Q - 1;
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & Q) {
+        X[0] ^= P;
+      } else {
+        const uint32_t t = (X[0] ^ X[i]) & P;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  X[1] ^= X[0];
+  X[2] ^= X[1];
+  uint32_t t = 0;
+  for (uint32_t Q = M; Q > 1; Q >>= 1)
+    if (X[2] & Q) t ^= Q - 1;
+  for (int i = 0; i < 3; ++i) X[i] ^= t;
+  uint64_t key = 0;
+  for (int b = bits - 1; b >= 0; --b)
+    for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> b) & 1u);
+  return key;
 }
 
-// Source slots of every cluster: particles in Morton order of their positions
-// (pos: n x 3 host), or in particle order when `sorted` is false.  Pad slots
+// Source slots of every cluster: particles in Hilbert-curve order of their
+// positions (pos: n x 3 host), or in particle order when `sorted` is false.  Pad slots
 // get -1.  sperm: S entries, sinv: N entries.
 void source_order(const double* pos, const int64_t* off, int32_t K, const int64_t* soff,
                   bool sorted, std::vector<int32_t>& sperm, std::vector<int32_t>& sinv) {
@@ -130,11 +153,12 @@ void source_order(const double* pos, const int64_t* off, int32_t K, const int64_
     for (int64_t i = 0; i < nk; ++i) {
       uint64_t code = 0;
       if (sorted) {
+        uint32_t u[3];
         for (int c = 0; c < 3; ++c) {
-          double q = (pos[3 * (n0 + i) + c] - lo[c]) / span * 2097151.0;
-          uint64_t u = (uint64_t)std::min(std::max(q, 0.0), 2097151.0);
-          code |= spread3(u) << c;
+          const double q = (pos[3 * (n0 + i) + c] - lo[c]) / span * 2097151.0;
+          u[c] = (uint32_t)std::min(std::max(q, 0.0), 2097151.0);
         }
+        code = hilbert_key(u[0], u[1], u[2], 21);
       }
       key[i] = {code, i};
     }
@@ -181,8 +205,8 @@ namespace {
 
 bool is_mixed(const nb_ctx* c) { return c->cfg.precision == NB_MIXED; }
 
-ForceArgs force_args(nb_ctx* c, const int32_t* active, double* acc, int sa, double* jerk, int sj,
-                     double* pot, int sp, bool f64_sources) {
+ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, double* acc, int sa,
+                     double* jerk, int sj, double* pot, int sp, bool f64_sources) {
   ForceArgs a{};
   a.off = c->d.off;
   a.soff = c->d.soff;
@@ -193,6 +217,8 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, double* acc, int sa, doub
   a.sinv = c->d.sinv;
   a.tiles = c->d.tiles;
   a.toff = c->d.toff;
+  a.rows = rows;
+  a.tile_counts = c->d.counters + 2;
   a.K = c->d.K;
   if (f64_sources) {
     a.src_a = c->d.src64_pos;
@@ -216,7 +242,7 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, double* acc, int sa, doub
 
 PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count) {
   PlanArgs p{};
-  p.NI = f64 ? kF64NI : kMixNI;
+  p.NI = f64 ? kF64NI : force_mixed_ni(c->cfg.variant);
   p.JT = f64 ? kF64JT : kMixJT;
   p.grid = f64 ? c->grid_f64 : c->grid_mix;
   p.forced_b = c->cfg.bfactor;
@@ -271,12 +297,12 @@ cudaError_t prof_events(nb_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
 
 // plan + force + partial reduce on the active list already described by
 // act_off (and `active`, or the identity when null).
-cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, double* acc, int sa, double* jerk,
-                          int sj, double* pot, int sp, bool f64, int step_mode, int count,
-                          bool pot_only, int64_t m_bound) {
+cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows, double* acc,
+                          int sa, double* jerk, int sj, double* pot, int sp, bool f64,
+                          int step_mode, int count, bool pot_only, int64_t m_bound) {
   cudaError_t e = launch_plan(c->d, plan_args(c, f64, step_mode, count), c->st);
   if (e != cudaSuccess) return e;
-  ForceArgs fa = force_args(c, active, acc, sa, jerk, sj, pot, sp, f64);
+  ForceArgs fa = force_args(c, active, rows, acc, sa, jerk, sj, pot, sp, f64);
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->prof) {
     e = prof_events(c, &ev);
@@ -294,7 +320,8 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, double* acc, int sa,
     if (e != cudaSuccess) return e;
     c->ev_pending.push_back(ev);
   }
-  return launch_reduce(fa, f64 ? kF64NI : kMixNI, !pot_only, m_bound, c->st);
+  return launch_reduce(fa, f64 ? kF64NI : force_mixed_ni(c->cfg.variant), !pot_only, m_bound,
+                       c->st);
 }
 
 cudaError_t enqueue_block_step(nb_ctx* c) {
@@ -309,7 +336,8 @@ cudaError_t enqueue_block_step(nb_ctx* c) {
   double* an = reinterpret_cast<double*>(c->d.acc_new);
   double* jn = reinterpret_cast<double*>(c->d.jerk_new);
   // the integrator needs no potential: the force kernel skips it here
-  e = enqueue_force(c, c->d.active, an, 4, jn, 4, nullptr, 0, f64, 1, 1, false, c->d.N);
+  e = enqueue_force(c, c->d.active, nullptr, an, 4, jn, 4, nullptr, 0, f64, 1, 1, false,
+                    c->d.N);
   if (e != cudaSuccess) return e;
   CorrectArgs ca{};
   ca.active = c->d.active;
@@ -363,7 +391,7 @@ void nb_default_config(nb_config* cfg) {
   cfg->bfactor = 0;
   cfg->graph_steps = 16;
   cfg->sort_sources = 1;
-  cfg->variant = 1;
+  cfg->variant = 2;
 }
 
 int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config* cfg, size_t* bytes) {
@@ -442,6 +470,8 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   d.n_tiles = n_tiles;
   d.sperm = reinterpret_cast<int32_t*>(w + c->L.sperm);
   d.sinv = reinterpret_cast<int32_t*>(w + c->L.sinv);
+  d.mark = reinterpret_cast<int32_t*>(w + c->L.mark);
+  d.rows = reinterpret_cast<int32_t*>(w + c->L.rows);
 
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -488,7 +518,8 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
         cudaMemsetAsync(d.acc, 0, 32 * N, st) || cudaMemsetAsync(d.jerk, 0, 32 * N, st) ||
         cudaMemsetAsync(d.t, 0, 8 * N, st) || cudaMemsetAsync(d.level, 0, 4 * N, st) ||
         cudaMemsetAsync(d.t_cur, 0, 8 * n_clusters, st) ||
-        cudaMemsetAsync(d.status, 0, 4, st) || cudaMemsetAsync(d.counters, 0, 32, st)) {
+        cudaMemsetAsync(d.status, 0, 4, st) || cudaMemsetAsync(d.counters, 0, 32, st) ||
+        cudaMemsetAsync(d.mark, 0xff, 4 * N, st)) {
       rc = NB_ECUDA;
       break;
     }
@@ -501,7 +532,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
     double* jn = reinterpret_cast<double*>(d.jerk_new);
     if (launch_predict(d, nullptr, 0, cfg->tick_exp, !f64, f64, false, st) ||
         launch_actoff_identity(d, st) ||
-        enqueue_force(c, nullptr, an, 4, jn, 4, an + 3, 4, f64, 0, 0, false, N) ||
+        enqueue_force(c, nullptr, nullptr, an, 4, jn, 4, an + 3, 4, f64, 0, 0, false, N) ||
         launch_init_levels(d, cfg->eta_start, cfg->tick_exp, cfg->level_min, cfg->level_max, st)) {
       rc = NB_ECUDA;
       break;
@@ -542,8 +573,9 @@ int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, doubl
   if (m == 0) return NB_OK;
   if (!active_idx || !acc || !jerk) return NB_EINVAL;
   const bool f64 = !is_mixed(c);
-  NB_TRY(launch_actoff_list(c->d, active_idx, m, c->st));
-  NB_TRY(enqueue_force(c, active_idx, acc, 3, jerk, 3, pot, 1, f64, 0, 1, false, m));
+  // targets in source-slot order (spatially coherent warps), rows mapped back
+  NB_TRY(launch_list_to_slots(c->d, active_idx, m, c->st));
+  NB_TRY(enqueue_force(c, c->d.active, c->d.rows, acc, 3, jerk, 3, pot, 1, f64, 0, 1, false, m));
   return NB_OK;
 }
 
@@ -615,7 +647,8 @@ int nb_energy(nb_ctx* c, int32_t cluster, double* ekin, double* epot) {
   double* an = reinterpret_cast<double*>(d.acc_new);
   NB_TRY(launch_predict(d, d.t_cur, 0, c->cfg.tick_exp, false, true, false, c->st));
   NB_TRY(launch_actoff_identity(d, c->st));
-  NB_TRY(enqueue_force(c, nullptr, nullptr, 0, nullptr, 0, an + 3, 4, true, 0, 0, true, d.N));
+  NB_TRY(enqueue_force(c, nullptr, nullptr, nullptr, 0, nullptr, 0, an + 3, 4, true, 0, 0, true,
+                       d.N));
   const int64_t lo = cluster < 0 ? 0 : c->off_host[cluster];
   const int64_t hi = cluster < 0 ? d.N : c->off_host[cluster + 1];
   double* out = d.esum + 2 * kEnergyBlocks;
@@ -718,6 +751,16 @@ int nb_profile_read(nb_ctx* c, double* force_ms, int64_t* launches) {
   if (launches) *launches = c->prof_launches;
   c->prof_ms = 0.0;
   c->prof_launches = 0;
+  return NB_OK;
+}
+
+int nb_tile_stats(nb_ctx* c, int64_t* warp_tiles, int64_t* near_warp_tiles) {
+  if (!c) return NB_EINVAL;
+  unsigned long long ctr[2];
+  NB_TRY(cudaMemcpyAsync(ctr, c->d.counters + 2, sizeof ctr, cudaMemcpyDeviceToHost, c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));
+  if (warp_tiles) *warp_tiles = (int64_t)ctr[0];
+  if (near_warp_tiles) *near_warp_tiles = (int64_t)ctr[1];
   return NB_OK;
 }
 

@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(NT) k_force_fp64(const ForceArgs a) {
       v[5] = (s.th[5] + s.tl[5]) - 3.0 * (s.th[8] + s.tl[8]);
       v[6] = -(s.th[9] + s.tl[9]);
       if (B == 1) {
-        const int64_t srow = a0 + q;
+        int64_t srow = a0 + q;
+        if (a.rows) srow = a.rows[srow];
         if (MODE == kF64Full) {
           if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[srow * a.sa + c] = a.G * v[c];
           if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[srow * a.sj + c] = a.G * v[3 + c];

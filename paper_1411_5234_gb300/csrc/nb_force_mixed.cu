@@ -1,11 +1,11 @@
 // nb_force_mixed.cu -- instantiation and launch of the mixed-precision force
 // kernel (the kernel itself is in nb_force_mixed.cuh).
 //
-// Shapes compiled in (selected per context; all handle kMixNI targets per
-// work item):
+// Shapes compiled in (selected per context by nb_config.variant; each
+// handles NT x IPT targets per work item):
 //   0: 128 threads x 2 targets, totals in registers, 1/s^2 = rsqrt^2
 //   1: 128 threads x 2 targets, totals in registers, 1/s^2 from the SFU
-//   2:  64 threads x 4 targets, totals in shared memory, 1/s^2 from the SFU
+//   2:  64 threads x 4 targets, totals in shared memory, 1/s^2 = rsqrt^2
 //   3: 256 threads x 1 target,  totals in registers, 1/s^2 from the SFU
 #include "nb_force_mixed.cuh"
 
@@ -13,7 +13,7 @@ namespace nb {
 namespace {
 template <bool POT> using S0 = mixk::MixShape<128, 2, POT, false, false, 2, 2>;
 template <bool POT> using S1 = mixk::MixShape<128, 2, POT, true, false, 2, 2>;
-template <bool POT> using S2 = mixk::MixShape<64, 4, POT, true, true, 1, 4>;
+template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 2, 4>;
 template <bool POT> using S3 = mixk::MixShape<256, 1, POT, true, false, 4, 2>;
 
 template <class Sh>
@@ -38,6 +38,15 @@ int occupancy_both() {
 }  // namespace
 
 int force_mixed_variants() { return 4; }
+
+int force_mixed_ni(int variant) {
+  switch (variant) {
+    case 1: return S1<false>::NI;
+    case 2: return S2<false>::NI;
+    case 3: return S3<false>::NI;
+    default: return S0<false>::NI;
+  }
+}
 
 cudaError_t launch_force_mixed(const ForceArgs& a, int grid, bool with_pot, int variant,
                                cudaStream_t st) {

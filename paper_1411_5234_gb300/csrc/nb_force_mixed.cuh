@@ -10,16 +10,20 @@
 // Precision (Sec. 2 item 4: DP resolution for the separations and the sums,
 // SP for the rest, square roots included).  Sources are stored relative to
 // the centre c_J of their tile of kMixJT spatially sorted slots, as
-// double-single offsets delta_j = dh_j + dl_j; a target's position relative to
-// the centre, e = c_J - r_i, is formed per tile in double-single (eh + el).
-//   * near tiles (some target of the warp within 2.5 tile radii h_J of c_J,
-//     the own tile included): d = (dh_j + eh) + (dl_j + el), FP64-like
+// double-single offsets delta_j = dh_j + dl_j from the centre c of their cell
+// (kMixJD consecutive slots, two cells per tile); a target's position
+// relative to the centre, e = c - r_i, is formed per cell in double-single
+// (eh + el).
+//   * near cells (some target of the warp within 2 cell radii h of the
+//     centre, the own cell included): d = (dh_j + eh) + (dl_j + el), FP64-like
 //     resolution for close pairs;
-//   * far tiles (every target of the warp beyond 2.5 h_J): d = dh_j + eh.
-//     With |e| >= 2 h_J, |d| >= |e| - h_J >= max(h_J, |e| / 2), so the three
-//     roundings (of dh_j, of eh, of the sum) stay within 4 units of 2^-24 |d|:
-//     the separation keeps the relative accuracy of the FP32 arithmetic
-//     after it, without the cancellation that absolute FP32 positions suffer.
+//   * far cells (every target of the warp beyond 2 h): d = dh_j + eh.  The
+//     three roundings (of dh_j, of eh, of the sum) are at most
+//     2^-24 (|delta_j| + |e| + |d|), and |e| <= |d| + |delta_j|, so the error
+//     stays within 4 units of 2^-24 |d| whenever |delta_j| <= |d|, which
+//     |e| > 2 h guarantees for every source of the cell: the separation keeps
+//     the relative accuracy of the FP32 arithmetic after it, without the
+//     cancellation that absolute FP32 positions suffer.
 // Everything after the separation is FP32 (hardware rsqrt and reciprocal);
 // sums are accumulated per tile in FP32 and folded into a compensated
 // (hi, lo) FP32 pair per tile (two-sum), then combined in FP64.
@@ -38,7 +42,7 @@
 //     shared-memory load.
 //
 // Shape parameters (MixShape): NT threads per CTA, IPT targets per thread
-// (NT * IPT == kMixNI), POT computes the potential, RCP takes 1/s^2 from the
+// (NT * IPT <= kMixNI targets per work item), POT computes the potential, RCP takes 1/s^2 from the
 // SFU reciprocal instead of an FP32 multiply, SMT keeps the compensated
 // totals in shared memory instead of registers, UNR unrolls the source loop,
 // MINB is the CTAs-per-SM hint of __launch_bounds__.
@@ -52,7 +56,10 @@ constexpr int JT = kMixJT;
 constexpr int kGroupF4 = 10;                      // float4 per group of 4 sources
 constexpr int kTileF4 = JT / 4 * kGroupF4;        // float4 per tile
 constexpr uint32_t kGroupBytes = kGroupF4 * 16;
-constexpr float kFarRatio2 = 2.5f * 2.5f;         // far: |e|^2 > (2.5 h)^2
+constexpr int kCellGroups = kMixJD / 4;           // groups of 4 sources per cell
+// far cell: |e| > 2 h, which gives |d| > h >= |delta_j| for every source of
+// the cell, the condition of the error bound above
+constexpr float kFarRatio2 = 4.0f;
 
 // component order inside a group of 4 sources (float4 index)
 enum { cDXH = 0, cDYH, cDZH, cM, cVX, cVY, cVZ, cDXL, cDYL, cDZL };
@@ -61,16 +68,34 @@ template <int NT_, int IPT_, bool POT_, bool RCP_, bool SMT_, int UNR_, int MINB
 struct MixShape {
   static constexpr int NT = NT_, IPT = IPT_, NI = NT_ * IPT_, UNR = UNR_, MINB = MINB_;
   static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_;
-  static_assert(NT_ * IPT_ == kMixNI, "targets per work item are fixed");
+  static_assert(NT_ * IPT_ <= kMixNI, "partial-sum rows hold at most kMixNI targets");
 };
 
+// What the source loop needs of one target in registers; the target's
+// absolute double-single position and its slot stay in shared memory.
 struct Target {
-  float xh, yh, zh, xl, yl, zl;                     // r_i, double-single
   f2 nvx, nvy, nvz;                                 // -v_i as broadcast pairs
   f2 ex, ey, ez;                                    // hi part of c_J - r_i (broadcast)
   f2 ax, ay, az, j1x, j1y, j1z, j2x, j2y, j2z, pt;  // per-tile sums (2 lanes)
-  int64_t slot;
 };
+
+// Per-thread shared-memory record of a target: r_i as double-single and its
+// source slot (-1: no target); component-major so a warp's loads are
+// conflict-free.
+template <int IPT, int NT>
+struct TargetPosSh {
+  float c[IPT][6][NT];
+  long long slot[IPT][NT];
+};
+struct TargetPos {
+  float xh, yh, zh, xl, yl, zl;
+  long long slot;
+};
+template <int IPT, int NT>
+__device__ __forceinline__ TargetPos load_tpos(const TargetPosSh<IPT, NT>& t, int r, int tid) {
+  return TargetPos{t.c[r][0][tid], t.c[r][1][tid], t.c[r][2][tid], t.c[r][3][tid],
+                   t.c[r][4][tid], t.c[r][5][tid], t.slot[r][tid]};
+}
 
 __device__ __forceinline__ f2 bcast(float v) { return f2_pack(v, v); }
 
@@ -89,27 +114,23 @@ __device__ __forceinline__ void ds_sub(float ah, float al, float bh, float bl, f
 // to the accumulators.
 template <class Sh, bool MASK>
 __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx, f2 wy, f2 wz,
-                                          f2 m, f2 eps2, int64_t js) {
+                                          f2 m, f2 eps2, int64_t js, int64_t slot) {
   f2 r2 = f2_fma(dx, dx, eps2);
   r2 = f2_fma(dy, dy, r2);
   r2 = f2_fma(dz, dz, r2);
   f2 rv = f2_mul(dx, wx);
   rv = f2_fma(dy, wy, rv);
   rv = f2_fma(dz, wz, rv);
-  const float2 q = f2_unpack(r2);
-  float ri0 = rsqrt_approx(q.x);
-  float ri1 = rsqrt_approx(q.y);
-  float rr0 = 0.f, rr1 = 0.f;
-  if (Sh::RCP) {
-    rr0 = rcp_approx(q.x);
-    rr1 = rcp_approx(q.y);
-  }
+  f2 rinv = f2_rsqrt(r2);
+  f2 rr = Sh::RCP ? f2_rcp(r2) : 0ull;
   if (MASK) {  // j == i is excluded by index (Eq. 1)
-    if (js == s.slot) ri0 = rr0 = 0.f;
-    if (js + 1 == s.slot) ri1 = rr1 = 0.f;
+    float2 a = f2_unpack(rinv), c = f2_unpack(rr);
+    if (js == slot) a.x = c.x = 0.f;
+    if (js + 1 == slot) a.y = c.y = 0.f;
+    rinv = f2_pack(a.x, a.y);
+    rr = f2_pack(c.x, c.y);
   }
-  const f2 rinv = f2_pack(ri0, ri1);
-  const f2 r2inv = Sh::RCP ? f2_pack(rr0, rr1) : f2_mul(rinv, rinv);
+  const f2 r2inv = Sh::RCP ? rr : f2_mul(rinv, rinv);
   const f2 mri = f2_mul(m, rinv);
   const f2 mr3 = f2_mul(mri, r2inv);
   if (Sh::POT) s.pt = f2_add(s.pt, mri);
@@ -126,12 +147,14 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
   s.j2z = f2_fma(bb, dz, s.j2z);
 }
 
-// Far tile: d = dh_j + eh.
-template <class Sh>
+// Far cell: d = dh_j + eh.  NG > 0: a full cell with a compile-time trip
+// count (no remainder code, better interleaving); NG == 0: ngroups groups.
+template <class Sh, int NG = 0>
 __device__ __forceinline__ void tile_far(const float4* __restrict__ tile, int ngroups,
                                          Target (&tg)[Sh::IPT], f2 eps2) {
+  const int n = NG > 0 ? NG : ngroups;
 #pragma unroll Sh::UNR
-  for (int g = 0; g < ngroups; ++g) {
+  for (int g = 0; g < n; ++g) {
     const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
                      vy = G[cVY], vz = G[cVZ];
@@ -140,39 +163,35 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ tile, int ng
       Target& s = tg[r];
       pair_tail<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
                            f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
-                           eps2, 0);
+                           eps2, 0, -1);
       pair_tail<Sh, false>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
                            f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
-                           eps2, 0);
+                           eps2, 0, -1);
     }
   }
 }
 
-// Near tile: d = (dh_j + eh) + (dl_j + el), el per target in registers here.
+// Near cell, one target: d = (dh_j + eh) + (dl_j + el).  Near cells are a
+// small fraction, so each target takes its own pass over the cell and only
+// one target's low parts are live at a time.
 template <class Sh, bool MASK>
-__device__ __forceinline__ void tile_near(const float4* __restrict__ tile, int ngroups,
-                                          int64_t slot0, Target (&tg)[Sh::IPT],
-                                          const f2 (&el)[Sh::IPT][3], f2 eps2) {
+__device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile, int ngroups,
+                                              int64_t slot0, Target& s, f2 elx, f2 ely, f2 elz,
+                                              int64_t slot, f2 eps2) {
 #pragma unroll 1
   for (int g = 0; g < ngroups; ++g) {
     const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
                      vy = G[cVY], vz = G[cVZ], dxl = G[cDXL], dyl = G[cDYL], dzl = G[cDZL];
     const int64_t js = slot0 + 4 * g;
-#pragma unroll
-    for (int r = 0; r < Sh::IPT; ++r) {
-      Target& s = tg[r];
-      pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.x, s.ex), f2_add(dxl.x, el[r][0])),
-                          f2_add(f2_add(dyh.x, s.ey), f2_add(dyl.x, el[r][1])),
-                          f2_add(f2_add(dzh.x, s.ez), f2_add(dzl.x, el[r][2])),
-                          f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
-                          eps2, js);
-      pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.y, s.ex), f2_add(dxl.y, el[r][0])),
-                          f2_add(f2_add(dyh.y, s.ey), f2_add(dyl.y, el[r][1])),
-                          f2_add(f2_add(dzh.y, s.ez), f2_add(dzl.y, el[r][2])),
-                          f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
-                          eps2, js + 2);
-    }
+    pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.x, s.ex), f2_add(dxl.x, elx)),
+                        f2_add(f2_add(dyh.x, s.ey), f2_add(dyl.x, ely)),
+                        f2_add(f2_add(dzh.x, s.ez), f2_add(dzl.x, elz)), f2_add(vx.x, s.nvx),
+                        f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x, eps2, js, slot);
+    pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.y, s.ex), f2_add(dxl.y, elx)),
+                        f2_add(f2_add(dyh.y, s.ey), f2_add(dyl.y, ely)),
+                        f2_add(f2_add(dzh.y, s.ez), f2_add(dzl.y, elz)), f2_add(vx.y, s.nvx),
+                        f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y, eps2, js + 2, slot);
   }
 }
 
@@ -227,24 +246,26 @@ __device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT>& T, flo
 }
 
 // Tile t0 .. t0 + cnt of the source slots (cnt a multiple of 4) plus its
-// (centre, radius) record.
+// cell records (centre, radius).
 __device__ __forceinline__ void issue_tile(float4* stage, float4* rec, uint64_t* bar,
                                            const float4* src, const float4* tiles,
                                            int64_t t0, int64_t cnt, int64_t tile_idx) {
   const uint32_t bytes = static_cast<uint32_t>(cnt / 4) * kGroupBytes;
-  mbar_arrive_expect(bar, bytes + 32u);
+  constexpr uint32_t rec_bytes = 16u * kTileRecF4;
+  mbar_arrive_expect(bar, bytes + rec_bytes);
   bulk_g2s(stage, src + (t0 >> 2) * kGroupF4, bytes, bar);
-  bulk_g2s(rec, tiles + 2 * tile_idx, 32u, bar);
+  bulk_g2s(rec, tiles + kTileRecF4 * tile_idx, rec_bytes, bar);
 }
 
 template <class Sh>
 __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArgs a) {
   constexpr int NT = Sh::NT, IPT = Sh::IPT, NI = Sh::NI;
   __shared__ __align__(128) float4 stage[2][kTileF4];
-  __shared__ __align__(16) float4 rec[2][2];
+  __shared__ __align__(16) float4 rec[2][kTileRecF4];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int abort_flag;
   __shared__ float tot_sh[Sh::SMT ? IPT * 20 * NT : 1];
+  __shared__ TargetPosSh<IPT, NT> tpos;
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -280,13 +301,17 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
     Target tg[IPT];
     Totals<Sh::SMT, NT> tot[IPT];
     bool valid[IPT];
+    // warp wp owns the 32 * IPT consecutive targets [wp * 32 * IPT, ...):
+    // target r of lane ln is wp * 32 * IPT + r * 32 + ln (spatially compact
+    // warps, coalesced rows per r)
+    const int wp = tid >> 5, ln = tid & 31;
 #pragma unroll
     for (int r = 0; r < IPT; ++r) {
-      const int32_t q = it * NI + r * NT + tid;
+      const int32_t q = it * NI + wp * 32 * IPT + r * 32 + ln;
       valid[r] = q < m_k;
       float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f, vx = 0.f, vy = 0.f,
             vz = 0.f;
-      tg[r].slot = -1;
+      long long slot_r = -1;
       if (valid[r]) {
         const int32_t s = a0 + q;
         const int64_t p = a.active ? (int64_t)a.active[s] : (int64_t)s;
@@ -297,8 +322,9 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
           const int64_t slot = a.sinv ? (int64_t)a.sinv[p] : sk0 + (p - p0);
           const float* gp =
               reinterpret_cast<const float*>(src + (slot >> 2) * kGroupF4) + (slot & 3);
-          // absolute position = own tile centre + offset, in double-single
-          const float4* tr = tiles + 2 * (tk0 + (slot - sk0) / JT);
+          // absolute position = own cell centre + offset, in double-single
+          const float4* tr = tiles + kTileRecF4 * (tk0 + (slot - sk0) / JT) +
+                             2 * (((slot - sk0) % JT) / kMixJD);
           const float4 ch = tr[0], cl = tr[1];
           ds_sub(ch.x, cl.x, -gp[4 * cDXH], -gp[4 * cDXL], xh, xl);
           ds_sub(ch.y, cl.y, -gp[4 * cDYH], -gp[4 * cDYL], yh, yl);
@@ -306,11 +332,16 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
           vx = gp[4 * cVX];
           vy = gp[4 * cVY];
           vz = gp[4 * cVZ];
-          tg[r].slot = slot;
+          slot_r = slot;
         }
       }
-      tg[r].xh = xh; tg[r].yh = yh; tg[r].zh = zh;
-      tg[r].xl = xl; tg[r].yl = yl; tg[r].zl = zl;
+      tpos.c[r][0][tid] = xh;
+      tpos.c[r][1][tid] = yh;
+      tpos.c[r][2][tid] = zh;
+      tpos.c[r][3][tid] = xl;
+      tpos.c[r][4][tid] = yl;
+      tpos.c[r][5][tid] = zl;
+      tpos.slot[r][tid] = slot_r;
       tg[r].nvx = bcast(-vx); tg[r].nvy = bcast(-vy); tg[r].nvz = bcast(-vz);
       tg[r].ax = tg[r].ay = tg[r].az = 0ull;
       tg[r].j1x = tg[r].j1y = tg[r].j1z = 0ull;
@@ -320,6 +351,7 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
     }
 
     const int64_t ntile = ceil_div64(j1 - j0, JT);
+    uint32_t n_near = 0;  // tiles this warp took on the near path
     if (tid == 0) {
       issue_tile(stage[0], rec[0], &bar[0], src, tiles, j0, min((int64_t)JT, j1 - j0),
                  tk0 + (j0 - sk0) / JT);
@@ -334,54 +366,64 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       const int st = static_cast<int>(t & 1);
       const int64_t t0 = j0 + t * JT;
       const int64_t cnt = min((int64_t)JT, j1 - t0);
-      const bool ok = mbar_wait(&bar[st], used[st] & 1u, kWaitBudget);
+      const bool ok_me = mbar_wait(&bar[st], used[st] & 1u, kWaitBudget);
       used[st] += 1;
       if (tid == 0) pending[st] = false;
-      if (!ok) {
+      if (!ok_me) {
         abort_flag = 1;
         atomicOr(a.status, kStatusTimeout);
       }
-      // every thread of the CTA reaches the vote below (ok is CTA-uniform in
-      // practice; a thread whose wait failed votes "near" and skips the work)
-      const float4 ch = rec[st][0], cl = rec[st][1];
-      const float far_lim = kFarRatio2 * ch.w * ch.w;
-      bool far = ok;
-      bool self = false;
+      // one decision for the whole CTA, so every thread takes the same path
+      // through the warp votes below
+      const bool ok = __syncthreads_and(ok_me) != 0;
+      const int ng = ok ? static_cast<int>(cnt >> 2) : 0;
+#pragma unroll 1
+      for (int q = 0; q < kMixCells; ++q) {
+        const int g0 = q * kCellGroups;
+        const int ngq = min(ng - g0, kCellGroups);
+        if (ngq <= 0) break;  // uniform: ng is the same in every thread
+        const float4 ch = rec[st][2 * q], cl = rec[st][2 * q + 1];
+        const float far_lim = kFarRatio2 * ch.w * ch.w;
+        bool far = true;
 #pragma unroll
-      for (int r = 0; r < IPT; ++r) {
-        float exh, exl, eyh, eyl, ezh, ezl;
-        ds_sub(ch.x, cl.x, tg[r].xh, tg[r].xl, exh, exl);
-        ds_sub(ch.y, cl.y, tg[r].yh, tg[r].yl, eyh, eyl);
-        ds_sub(ch.z, cl.z, tg[r].zh, tg[r].zl, ezh, ezl);
-        tg[r].ex = bcast(exh);
-        tg[r].ey = bcast(eyh);
-        tg[r].ez = bcast(ezh);
-        const float d2 = exh * exh + eyh * eyh + ezh * ezh;
-        far = far && (!valid[r] || d2 > far_lim);
-        self |= (tg[r].slot >= t0) && (tg[r].slot < t0 + cnt);
-      }
-      const bool warp_far = __all_sync(0xffffffffu, far);
-      if (ok) {
-        const int ng = static_cast<int>(cnt >> 2);
-        if (warp_far) {
-          tile_far<Sh>(stage[st], ng, tg, eps2);
+        for (int r = 0; r < IPT; ++r) {
+          const TargetPos tp = load_tpos(tpos, r, tid);
+          float exh, exl, eyh, eyl, ezh, ezl;
+          ds_sub(ch.x, cl.x, tp.xh, tp.xl, exh, exl);
+          ds_sub(ch.y, cl.y, tp.yh, tp.yl, eyh, eyl);
+          ds_sub(ch.z, cl.z, tp.zh, tp.zl, ezh, ezl);
+          tg[r].ex = bcast(exh);
+          tg[r].ey = bcast(eyh);
+          tg[r].ez = bcast(ezh);
+          const float d2 = exh * exh + eyh * eyh + ezh * ezh;
+          far = far && (!valid[r] || d2 > far_lim);
+        }
+        const float4* cell = stage[st] + g0 * kGroupF4;
+        const int64_t c0 = t0 + 4 * g0;
+        if (__all_sync(0xffffffffu, far)) {
+          if (ngq == kCellGroups)
+            tile_far<Sh, kCellGroups>(cell, ngq, tg, eps2);
+          else
+            tile_far<Sh>(cell, ngq, tg, eps2);
         } else {
-          f2 el[IPT][3];
+          ++n_near;
 #pragma unroll
           for (int r = 0; r < IPT; ++r) {
-            float h, lo;
-            ds_sub(ch.x, cl.x, tg[r].xh, tg[r].xl, h, lo);
-            el[r][0] = bcast(lo);
-            ds_sub(ch.y, cl.y, tg[r].yh, tg[r].yl, h, lo);
-            el[r][1] = bcast(lo);
-            ds_sub(ch.z, cl.z, tg[r].zh, tg[r].zl, h, lo);
-            el[r][2] = bcast(lo);
+            const TargetPos tp = load_tpos(tpos, r, tid);
+            float h, lx, ly, lz;
+            ds_sub(ch.x, cl.x, tp.xh, tp.xl, h, lx);
+            ds_sub(ch.y, cl.y, tp.yh, tp.yl, h, ly);
+            ds_sub(ch.z, cl.z, tp.zh, tp.zl, h, lz);
+            if (tp.slot >= c0 && tp.slot < c0 + 4 * ngq)  // the target's own cell
+              tile_near_one<Sh, true>(cell, ngq, c0, tg[r], bcast(lx), bcast(ly), bcast(lz),
+                                      tp.slot, eps2);
+            else
+              tile_near_one<Sh, false>(cell, ngq, c0, tg[r], bcast(lx), bcast(ly), bcast(lz),
+                                       -1, eps2);
           }
-          if (self)
-            tile_near<Sh, true>(stage[st], ng, t0, tg, el, eps2);
-          else
-            tile_near<Sh, false>(stage[st], ng, t0, tg, el, eps2);
         }
+      }
+      if (ok) {
 #pragma unroll
         for (int r = 0; r < IPT; ++r) flush<Sh>(tg[r], tot[r], tot_sh + r * 20 * NT + tid);
       }
@@ -394,6 +436,10 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       }
     }
 
+    if (ln == 0 && a.tile_counts) {
+      atomicAdd(a.tile_counts, (unsigned long long)ceil_div64(j1 - j0, kMixJD));
+      atomicAdd(a.tile_counts + 1, (unsigned long long)n_near);
+    }
 #pragma unroll
     for (int r = 0; r < IPT; ++r) {
       if (!valid[r]) continue;
@@ -406,9 +452,10 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       v[4] = tot[r].get(col, 4) - 3.0 * tot[r].get(col, 7);
       v[5] = tot[r].get(col, 5) - 3.0 * tot[r].get(col, 8);
       v[6] = Sh::POT ? -tot[r].get(col, 9) : 0.0;
-      const int32_t ql = r * NT + tid;
+      const int32_t ql = wp * 32 * IPT + r * 32 + ln;
       if (B == 1) {
-        const int64_t srow = a0 + it * NI + ql;
+        int64_t srow = a0 + it * NI + ql;
+        if (a.rows) srow = a.rows[srow];
         if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[srow * a.sa + c] = a.G * v[c];
         if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[srow * a.sj + c] = a.G * v[3 + c];
         if (Sh::POT && a.out_pot) a.out_pot[srow * a.sp] = a.G * v[6];

@@ -144,7 +144,7 @@ __global__ void k_scan(Dev d, int32_t nblk) {
 __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* t_tgt,
                                                           int64_t t_fixed, int T, int write_mix,
                                                           int write64, int count_due) {
-  __shared__ double shd[32];
+  __shared__ double shd[kMixJT / 32];
   __shared__ int32_t shi[32];
   const int32_t tile = blockIdx.x;
   const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
@@ -290,11 +290,12 @@ __global__ void k_reduce(ForceArgs a, int NI, int with_acc) {
 #pragma unroll
       for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
     }
+    const int64_t row = a.rows ? (int64_t)a.rows[s] : (int64_t)s;
     if (with_acc) {
-      if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[(int64_t)s * a.sa + c] = a.G * v[c];
-      if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[(int64_t)s * a.sj + c] = a.G * v[3 + c];
+      if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[row * a.sa + c] = a.G * v[c];
+      if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[row * a.sj + c] = a.G * v[3 + c];
     }
-    if (a.out_pot) a.out_pot[(int64_t)s * a.sp] = a.G * v[6];
+    if (a.out_pot) a.out_pot[row * a.sp] = a.G * v[6];
   }
 }
 
@@ -402,24 +403,52 @@ __global__ void k_init_levels(Dev d, double eta_s, int T, int lmin, int lmax) {
   }
 }
 
-// Cluster offsets of a caller's active list (lower bounds of the cluster
-// starts) and its validation: strictly ascending, inside [0, N).
-__global__ void k_actoff_list(Dev d, const int32_t* list, int64_t m) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s = tid; s < m; s += nth) {
-    const int32_t v = list[s];
-    if (v < 0 || v >= d.N || (s + 1 < m && list[s + 1] <= v)) atomicOr(d.status, kStatusInval);
-  }
-  for (int64_t k = tid; k <= d.K; k += nth) {
-    const int64_t key = d.off[k];
-    int64_t lo = 0, hi = m;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if ((int64_t)list[mid] < key) lo = mid + 1; else hi = mid;
+// A caller's target list: mark[p] = its row k (list[k] = p), checking that
+// every entry lies in [0, N) and appears once.  mark must hold -1 before.
+__global__ void k_mark_list(Dev d, const int32_t* list, int64_t m) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = list[k];
+    if (p < 0 || p >= d.N) {
+      atomicOr(d.status, kStatusInval);
+      continue;
     }
-    d.act_off[k] = static_cast<int32_t>(k == d.K ? m : lo);
+    if (atomicExch(d.mark + p, static_cast<int32_t>(k)) != -1) atomicOr(d.status, kStatusInval);
   }
+}
+
+// Marked particles per source tile (one CTA of kMixJT threads per tile).
+__global__ void __launch_bounds__(kMixJT) k_count_marked(Dev d) {
+  __shared__ int32_t sh[32];
+  const int32_t tile = blockIdx.x;
+  const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
+  const int64_t s = d.soff[k] + (int64_t)(tile - d.toff[k]) * kMixJT + threadIdx.x;
+  const int32_t p = s < d.soff[k + 1] ? d.sperm[s] : -1;
+  const int32_t f = (p >= 0 && d.mark[p] >= 0) ? 1 : 0;
+  const int32_t tot =
+      block_reduce<int32_t>(f, [](int32_t x, int32_t y) { return x + y; }, sh, 0);
+  if (threadIdx.x == 0) d.blk_count[tile] = tot;
+}
+
+// The marked particles in source-slot order (spatially coherent targets),
+// their caller rows, each cluster's offset in the list; clears the marks.
+__global__ void __launch_bounds__(kMixJT) k_scatter_marked(Dev d) {
+  __shared__ int32_t sh[32];
+  const int32_t tile = blockIdx.x;
+  const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
+  const int64_t s = d.soff[k] + (int64_t)(tile - d.toff[k]) * kMixJT + threadIdx.x;
+  const int32_t p = s < d.soff[k + 1] ? d.sperm[s] : -1;
+  const int32_t row = p >= 0 ? d.mark[p] : -1;
+  const int32_t f = row >= 0 ? 1 : 0;
+  int32_t tot;
+  const int32_t ex = block_excl_scan(f, sh, &tot);
+  const int32_t run = d.blk_count[tile];
+  if (f) {
+    d.active[run + ex] = p;
+    d.rows[run + ex] = row;
+    d.mark[p] = -1;
+  }
+  if (s == d.soff[k]) d.act_off[k] = run;
 }
 
 // Identity active list: every particle of every cluster is a target.
@@ -536,8 +565,12 @@ cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int 
   k_init_levels<<<blocks_for(d.N, 256), 256, 0, st>>>(d, eta_s, T, lmin, lmax);
   return cudaGetLastError();
 }
-cudaError_t launch_actoff_list(const Dev& d, const int32_t* list, int64_t m, cudaStream_t st) {
-  k_actoff_list<<<blocks_for(m > d.K ? m : d.K + 1, 256), 256, 0, st>>>(d, list, m);
+cudaError_t launch_list_to_slots(const Dev& d, const int32_t* list, int64_t m,
+                                 cudaStream_t st) {
+  k_mark_list<<<blocks_for(m, 256), 256, 0, st>>>(d, list, m);
+  k_count_marked<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d);
+  k_scan<<<1, 1024, 0, st>>>(d, static_cast<int32_t>(d.n_tiles));
+  k_scatter_marked<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d);
   return cudaGetLastError();
 }
 cudaError_t launch_actoff_identity(const Dev& d, cudaStream_t st) {

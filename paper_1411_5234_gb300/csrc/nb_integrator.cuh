@@ -6,45 +6,42 @@
 
 namespace nb {
 
-// Write one mixed source tile (one CTA of kMixJT threads, one slot each):
-// centre c = midpoint of the valid particles' bounding box, rounded to a
-// double-single pair (ch, cl); radius h = max |r_j - c| (rounded up); each
-// valid slot stores its double-single offset r_j - c, mass and FP32
-// velocity; pad slots (in == true, valid == false) hold massless dummies far
-// away.  `sh` is 32 doubles of shared scratch.  Every thread must call this.
-__device__ __forceinline__ double nb_block_reduce_d(double v, bool is_max, double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Min or max of v over the threads of one cell (kMixJD = 64 threads, two
+// warps) of a CTA of kMixJT threads; every thread gets its cell's result.
+// `sh` holds >= kMixJT / 32 doubles.
+__device__ __forceinline__ double nb_half_reduce_d(double v, bool is_max, double* sh) {
+  static_assert(kMixJD == 64 && kMixJT % kMixJD == 0, "two warps per cell");
   for (int o = 16; o > 0; o >>= 1) {
-    const double u = __shfl_down_sync(0xffffffffu, v, o);
+    const double u = __shfl_xor_sync(0xffffffffu, v, o);
     v = is_max ? fmax(v, u) : fmin(v, u);
   }
-  if (lane == 0) sh[wid] = v;
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh[wid] = v;
   __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    v = lane < nw ? sh[lane] : (is_max ? -CUDART_INF : CUDART_INF);
-    for (int o = 16; o > 0; o >>= 1) {
-      const double u = __shfl_down_sync(0xffffffffu, v, o);
-      v = is_max ? fmax(v, u) : fmin(v, u);
-    }
-    if (lane == 0) sh[0] = v;
-  }
+  const double a = sh[wid & ~1], b = sh[wid | 1];
   __syncthreads();
-  const double r = sh[0];
-  __syncthreads();
-  return r;
+  return is_max ? fmax(a, b) : fmin(a, b);
 }
 
+// Write one mixed source tile (one CTA of kMixJT threads, one slot each).
+// The tile holds kMixCells cells of kMixJD slots; for each cell: centre c = the
+// midpoint of its valid particles' bounding box, rounded to a double-single
+// pair (ch, cl), radius h = max |r_j - c| (rounded up).  Each valid slot
+// stores its double-single offset r_j - c from its cell's centre, its mass
+// and FP32 velocity; pad slots (in == true, valid == false) hold massless
+// dummies far away.  Record of tile t: float4 [kTileRecF4 t + 2q] = (ch, h)
+// and [kTileRecF4 t + 2q + 1] = (cl, 0) for cell q.  Every thread must call
+// this.
 __device__ __forceinline__ void build_mixed_tile(float4* src, float4* tiles, int64_t tile,
                                                  int64_t s, bool in, bool valid, double3 x,
                                                  double m, double3 v, double* sh) {
   const double inf = CUDART_INF;
-  const double lx = nb_block_reduce_d(valid ? x.x : inf, false, sh);
-  const double ly = nb_block_reduce_d(valid ? x.y : inf, false, sh);
-  const double lz = nb_block_reduce_d(valid ? x.z : inf, false, sh);
-  const double hx = nb_block_reduce_d(valid ? x.x : -inf, true, sh);
-  const double hy = nb_block_reduce_d(valid ? x.y : -inf, true, sh);
-  const double hz = nb_block_reduce_d(valid ? x.z : -inf, true, sh);
+  const double lx = nb_half_reduce_d(valid ? x.x : inf, false, sh);
+  const double ly = nb_half_reduce_d(valid ? x.y : inf, false, sh);
+  const double lz = nb_half_reduce_d(valid ? x.z : inf, false, sh);
+  const double hx = nb_half_reduce_d(valid ? x.x : -inf, true, sh);
+  const double hy = nb_half_reduce_d(valid ? x.y : -inf, true, sh);
+  const double hz = nb_half_reduce_d(valid ? x.z : -inf, true, sh);
   const bool any = lx <= hx;
   const double cx = any ? 0.5 * (lx + hx) : 0.0, cy = any ? 0.5 * (ly + hy) : 0.0,
                cz = any ? 0.5 * (lz + hz) : 0.0;
@@ -55,7 +52,7 @@ __device__ __forceinline__ void build_mixed_tile(float4* src, float4* tiles, int
                uz = (double)chz + (double)clz;  // the centre as represented
   const double dx = x.x - ux, dy = x.y - uy, dz = x.z - uz;
   const double r = valid ? sqrt(dx * dx + dy * dy + dz * dz) : 0.0;
-  const double h = nb_block_reduce_d(r, true, sh);
+  const double h = nb_half_reduce_d(r, true, sh);
   if (in) {
     float* g = reinterpret_cast<float*>(src + (s >> 2) * 10) + (s & 3);
     if (valid) {
@@ -78,9 +75,10 @@ __device__ __forceinline__ void build_mixed_tile(float4* src, float4* tiles, int
       g[28] = g[32] = g[36] = 0.f;
     }
   }
-  if (threadIdx.x == 0) {
-    tiles[2 * tile] = make_float4(chx, chy, chz, __double2float_ru(h));
-    tiles[2 * tile + 1] = make_float4(clx, cly, clz, 0.f);
+  if ((threadIdx.x & (kMixJD - 1)) == 0) {
+    const int q = threadIdx.x / kMixJD;
+    tiles[kTileRecF4 * tile + 2 * q] = make_float4(chx, chy, chz, __double2float_ru(h));
+    tiles[kTileRecF4 * tile + 2 * q + 1] = make_float4(clx, cly, clz, 0.f);
   }
 }
 
@@ -118,7 +116,8 @@ cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_b
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st);
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,
                                cudaStream_t st);
-cudaError_t launch_actoff_list(const Dev& d, const int32_t* list, int64_t m, cudaStream_t st);
+// caller list -> d.active (slot order), d.rows (caller rows), act_off
+cudaError_t launch_list_to_slots(const Dev& d, const int32_t* list, int64_t m, cudaStream_t st);
 cudaError_t launch_actoff_identity(const Dev& d, cudaStream_t st);
 cudaError_t launch_energy(const Dev& d, const double* pot, int sp, int64_t lo, int64_t hi,
                           double* part, int nblk, double* out, cudaStream_t st);

@@ -35,6 +35,9 @@ constexpr int kMixNT = 128;          // threads per CTA
 constexpr int kMixIPT = 2;           // targets (i) per thread
 constexpr int kMixNI = kMixNT * kMixIPT;
 constexpr int kMixJT = 128;          // sources per shared-memory tile (multiple of 4)
+constexpr int kMixJD = 64;           // sources per cell (one centre/radius record)
+constexpr int kMixCells = kMixJT / kMixJD;  // cells per tile
+constexpr int kTileRecF4 = 2 * kMixCells;   // float4 of cell records per tile
 // FP64 force kernel shape.
 constexpr int kF64NT = 128;
 constexpr int kF64NI = kF64NT;
@@ -55,11 +58,13 @@ struct Dev {
   int32_t* active = nullptr;
   dbl4 *acc_new = nullptr, *jerk_new = nullptr;
   float4* src_mix = nullptr;     // (S / 4) * 10 float4
-  float4* tiles = nullptr;       // 2 float4 per mixed source tile: (c_hi, h), (c_lo, 0)
+  float4* tiles = nullptr;       // kTileRecF4 float4 per mixed source tile: per cell (c_hi, h), (c_lo, 0)
   int32_t* toff = nullptr;       // K + 1: first tile of each cluster
   int64_t n_tiles = 0;
   int32_t* sperm = nullptr;      // S: particle of each source slot (-1: pad)
   int32_t* sinv = nullptr;       // N: source slot of each particle
+  int32_t* mark = nullptr;       // N: caller row of each listed particle (-1: none)
+  int32_t* rows = nullptr;       // N: caller row of each target in slot order
   dbl4* src64_pos = nullptr;  // S
   dbl4* src64_vel = nullptr;  // S
   double* partials = nullptr;    // part_items * 7 * NI_max
@@ -72,6 +77,7 @@ struct Dev {
   double* esum = nullptr;        // energy partial sums
   uint32_t* status = nullptr;
   unsigned long long* counters = nullptr;  // [0] interactions [1] block steps
+                                           // [2] warp-tiles [3] near warp-tiles
   int64_t* t_end = nullptr;      // 1
 };
 
@@ -86,6 +92,8 @@ struct ForceArgs {
   const int32_t* sinv;      // source slot of each particle (nullptr: slot order = particle order)
   const float4* tiles;      // mixed source tile records
   const int32_t* toff;      // first tile of each cluster (K + 1)
+  const int32_t* rows;      // output row of each target (nullptr: its position in the list)
+  unsigned long long* tile_counts;  // [0] warp-tiles, [1] of them near (nullptr: not counted)
   int32_t K;
   const void* src_a;        // mixed: float4 groups; FP64: positions
   const void* src_b;        // FP64: velocities
@@ -189,6 +197,31 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// SFU on both lanes of a pair, results written straight into the pair's
+// halves (one asm block, so no register moves are needed to repack them).
+__device__ __forceinline__ f2 f2_rsqrt(f2 x) {
+  f2 y;
+  asm("{\n\t.reg .f32 a, b;\n\t"
+      "mov.b64 {a, b}, %1;\n\t"
+      "rsqrt.approx.ftz.f32 a, a;\n\t"
+      "rsqrt.approx.ftz.f32 b, b;\n\t"
+      "mov.b64 %0, {a, b};\n\t}"
+      : "=l"(y)
+      : "l"(x));
+  return y;
+}
+__device__ __forceinline__ f2 f2_rcp(f2 x) {
+  f2 y;
+  asm("{\n\t.reg .f32 a, b;\n\t"
+      "mov.b64 {a, b}, %1;\n\t"
+      "rcp.approx.ftz.f32 a, a;\n\t"
+      "rcp.approx.ftz.f32 b, b;\n\t"
+      "mov.b64 %0, {a, b};\n\t}"
+      : "=l"(y)
+      : "l"(x));
+  return y;
+}
+
 // Knuth's error-free two-sum: hi + lo accumulates x exactly up to the final
 // rounding of lo.
 template <typename T>
@@ -226,6 +259,7 @@ cudaError_t launch_force_mixed(const ForceArgs& a, int grid, bool with_pot, int 
                                cudaStream_t st);
 cudaError_t launch_force_fp64(const ForceArgs& a, int grid, int mode, cudaStream_t st);
 int force_mixed_variants();
+int force_mixed_ni(int variant);  // targets per work item of a mixed shape
 int force_mixed_ctas_per_sm(int variant);
 int force_fp64_ctas_per_sm();
 size_t force_mixed_smem();

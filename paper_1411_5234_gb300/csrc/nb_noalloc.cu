@@ -11,7 +11,7 @@
 // device array compiled into the library.
 //
 // Properties a caller must know:
-//   * the array is kNoAllocBytes (6,697,472) bytes, lives on every GPU that loads the
+//   * the array is kNoAllocBytes (6,705,664) bytes, lives on every GPU that loads the
 //     library, and is held until the process exits;
 //   * at most NB_NOALLOC_MAX_SOURCES sources per call; larger calls are
 //     rejected with NB_EINVAL before anything is launched;
@@ -45,11 +45,11 @@ constexpr size_t kOffPartials = kOffSources + kSourceBytes;
 constexpr size_t kPartialBytes = align_up((size_t)kNoAllocItems * kPartialComps * kMixNI * 8);
 constexpr int64_t kNoAllocTiles = (kNoAllocSlots + kMixJT - 1) / kMixJT;
 constexpr size_t kOffTiles = kOffPartials + kPartialBytes;
-constexpr size_t kTileBytes = align_up(32 * (size_t)kNoAllocTiles);
+constexpr size_t kTileBytes = align_up(16 * kTileRecF4 * (size_t)kNoAllocTiles);
 constexpr size_t kOffSmall = kOffTiles + kTileBytes;
 constexpr size_t kSmallBytes = 4096;  // offsets, plan words, status, counters
-constexpr size_t kNoAllocBytes = kOffSmall + kSmallBytes;  // 6,697,472 bytes
-static_assert(kNoAllocBytes == 6697472, "documented size of the fixed array");
+constexpr size_t kNoAllocBytes = kOffSmall + kSmallBytes;  // 6,705,664 bytes
+static_assert(kNoAllocBytes == 6705664, "documented size of the fixed array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kMixJT) k_noalloc_pack_mix(const double* pos, 
                                                              const double* mass, int64_t n,
                                                              int64_t n_pad, float4* src,
                                                              float4* tiles) {
-  __shared__ double sh[32];
+  __shared__ double sh[kMixJT / 32];
   const int64_t s = (int64_t)blockIdx.x * kMixJT + threadIdx.x;
   const bool in = s < n_pad, valid = s < n;
   double3 x = make_double3(0.0, 0.0, 0.0), v = make_double3(0.0, 0.0, 0.0);
@@ -193,9 +193,9 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
                                                    d.tiles);
   if (cudaGetLastError() != cudaSuccess) return NB_ECUDA;
 
-  const int grid = ds->sms * (f64 ? force_fp64_ctas_per_sm() : force_mixed_ctas_per_sm(1));
+  const int grid = ds->sms * (f64 ? force_fp64_ctas_per_sm() : force_mixed_ctas_per_sm(2));
   PlanArgs p{};
-  p.NI = f64 ? kF64NI : kMixNI;
+  p.NI = f64 ? kF64NI : force_mixed_ni(2);
   p.JT = f64 ? kF64JT : kMixJT;
   p.grid = grid;
   p.forced_b = 0;
@@ -214,6 +214,8 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   a.sinv = nullptr;  // sources in particle order
   a.tiles = d.tiles;
   a.toff = d.toff;
+  a.rows = nullptr;
+  a.tile_counts = nullptr;
   a.K = 1;
   a.src_a = f64 ? static_cast<const void*>(d.src64_pos) : static_cast<const void*>(d.src_mix);
   a.src_b = f64 ? d.src64_vel : nullptr;
@@ -228,7 +230,7 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   a.eps2 = eps * eps;
   a.status = d.status;
   cudaError_t e = f64 ? launch_force_fp64(a, grid, kF64Full, st)
-                      : launch_force_mixed(a, grid, pot != nullptr, 1, st);
+                      : launch_force_mixed(a, grid, pot != nullptr, 2, st);
   if (e != cudaSuccess) return NB_ECUDA;
   if (launch_reduce(a, p.NI, true, m, st) != cudaSuccess) return NB_ECUDA;
   return NB_OK;

@@ -23,7 +23,7 @@ FUNCTIONS = [
     "nb_default_config", "nb_workspace_size", "nb_init", "nb_free", "nb_predict", "nb_force",
     "nb_correct", "nb_step_block", "nb_set_end_time", "nb_energy", "nb_get_state",
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
-    "nb_profile_enable", "nb_profile_read", "nb_force_noalloc",
+    "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
 ]
 
 
@@ -72,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "nb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "nb_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "nb_profile_read": (ctypes.c_int, [P, P, P]),
+        "nb_tile_stats": (ctypes.c_int, [P, P, P]),
         "nb_force_noalloc": (ctypes.c_int, [P, P, P, i64, P, i64, ctypes.c_double,
                                             ctypes.c_double, i32, P, P, P, P]),
     }
@@ -267,6 +268,12 @@ class Sim:
         _check(lib.nb_get_state(self._ctx, *[None if a is None else _hptr(a)
                                              for a in (pos, vel, acc, jerk, t, level)]),
                "nb_get_state")
+
+    def tile_stats(self):
+        """(warp-tiles, of which near) of the mixed force kernel since nb_init."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.nb_tile_stats(self._ctx, ctypes.byref(a), ctypes.byref(b)), "nb_tile_stats")
+        return a.value, b.value
 
     def status(self) -> int:
         return int(lib.nb_status(self._ctx))

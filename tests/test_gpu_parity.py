@@ -6,10 +6,17 @@ Tolerances:
     order and uses CUDA's rsqrt, so agreement is to a few ulps times the
     conditioning sum|terms| / |sum|).
   * mixed path: FP32 pair arithmetic (24-bit mantissa, hardware rsqrt with
-    ~2^-22.9 relative error) on FP64-resolution separations: the per-term error
-    is a few 1e-7, so the per-particle force error is bounded by a few 1e-7
-    times the conditioning; gated at 1e-6 for the 99.9th percentile and 1e-5
-    for the worst particle, with the jerk at 4x those.
+    ~2^-22.9 relative error) on separations accurate to a few ulp: every
+    term carries a relative error of a few 2^-24, so the error of a sum is
+    bounded by that times sum_j |term_j|, not times |sum|.  Worst case per
+    term: the separation carries <= 4 ulp (far cells), which the direction
+    and the cube of the length turn into <= 16 ulp of m d / s^3, plus ~3 ulp
+    from rsqrt^3 and the products: ~22 ulp = 1.3e-6.  Gated per particle on
+    the condition-scaled error ||da_i|| / sum_j |a_ij| <= 1e-6 (jerk, with its
+    own terms and more products: <= 3e-6), plus, for samples of >= 100
+    targets, the plain relative error's median <= 1e-7 and, for >= 1000
+    targets, its 99.9th percentile <= 1e-6 for the acceleration (jerk:
+    median <= 5e-7, 99.9th percentile <= 4e-6).
 """
 import math
 
@@ -25,6 +32,39 @@ pytestmark = pytest.mark.gpu
 
 def rel_err(x, ref):
     return np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def term_sums(cl, eps, idx, G=1.0):
+    """sum_j |a_ij| and sum_j |jerk_ij| (component-wise norms) per target."""
+    idx = np.asarray(idx)
+    Sa = np.empty(len(idx))
+    Sj = np.empty(len(idx))
+    for c0 in range(0, len(idx), 256):
+        ii = idx[c0:c0 + 256]
+        d = cl.pos[None, :, :] - cl.pos[ii, None, :]
+        w = cl.vel[None, :, :] - cl.vel[ii, None, :]
+        s2 = (d * d).sum(2) + eps * eps
+        s2[np.arange(len(ii)), ii] = np.inf            # j == i excluded
+        inv3 = s2 ** -1.5
+        m = G * cl.mass[None, :]
+        Sa[c0:c0 + 256] = (m * np.sqrt((d * d).sum(2)) * inv3).sum(1)
+        dw = np.abs((d * w).sum(2))
+        Sj[c0:c0 + 256] = (m * (np.sqrt((w * w).sum(2)) * inv3
+                               + 3 * dw * np.sqrt((d * d).sum(2)) * inv3 / s2)).sum(1)
+    return Sa, Sj
+
+
+def check_mixed(a, j, ra, rj, Sa, Sj):
+    ea, ej = rel_err(a, ra), rel_err(j, rj)
+    ca = np.linalg.norm(a - ra, axis=1) / Sa
+    cj = np.linalg.norm(j - rj, axis=1) / Sj
+    assert ca.max() <= 1e-6, ca.max()
+    assert cj.max() <= 3e-6, cj.max()
+    if len(ea) >= 100:      # distribution gates need a population
+        assert np.median(ea) <= 1e-7 and np.median(ej) <= 5e-7, (np.median(ea), np.median(ej))
+    if len(ea) >= 1000:
+        assert np.quantile(ea, 0.999) <= 1e-6, np.quantile(ea, 0.999)
+        assert np.quantile(ej, 0.999) <= 4e-6, np.quantile(ej, 0.999)
 
 
 def gpu_force(nb, cl, eps, idx, prec, bfactor=0, G=1.0):
@@ -78,9 +118,7 @@ def test_mixed_force_parity(nb, n, m):
     idx = inputs.random_active(n, mm, seed=3)
     a, j, p = gpu_force(nb, cl, 1e-4, idx, nb.NB_MIXED)
     ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx)
-    ea, ej = rel_err(a, ra), rel_err(j, rj)
-    assert np.quantile(ea, 0.999) <= 1e-6 and ea.max() <= 1e-5, (ea.max(), np.median(ea))
-    assert np.quantile(ej, 0.999) <= 4e-6 and ej.max() <= 4e-5, (ej.max(), np.median(ej))
+    check_mixed(a, j, ra, rj, *term_sums(cl, 1e-4, idx))
     assert np.abs(p / rp - 1).max() <= 1e-6
 
 
@@ -126,6 +164,20 @@ def test_bfactor_invariance(nb):
             assert rel_err(x, r).max() <= 1e-6
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_target_order_is_free(nb, prec):
+    # rows follow the caller's list whatever its order; values do not depend
+    # on it beyond the summation order inside the kernel (identical here)
+    P = nb.NB_FP64 if prec == "fp64" else nb.NB_MIXED
+    cl = inputs.plummer(3001, seed=31, imf="kroupa")
+    idx = inputs.random_active(3001, 700, seed=2)
+    perm = np.random.default_rng(0).permutation(700)
+    a1, j1, p1 = gpu_force(nb, cl, 1e-4, idx, P)
+    a2, j2, p2 = gpu_force(nb, cl, 1e-4, idx[perm], P)
+    assert np.array_equal(a2, a1[perm]) and np.array_equal(j2, j1[perm])
+    assert np.array_equal(p2, p1[perm])
+
+
 def test_force_empty_and_invalid_lists(nb, plummer1024):
     cl = plummer1024
     sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nb.NB_FP64)
@@ -133,8 +185,8 @@ def test_force_empty_and_invalid_lists(nb, plummer1024):
     empty = torch.empty(0, dtype=torch.int32, device="cuda")
     sim.force(empty)
     assert sim.status() == nb.NB_OK
-    bad = torch.tensor([5, 3, 9], dtype=torch.int32, device="cuda")  # not ascending
-    sim.force(bad)
+    rep = torch.tensor([5, 3, 9, 3], dtype=torch.int32, device="cuda")  # repeated entry
+    sim.force(rep)
     assert sim.status() == nb.NB_EINVAL
     sim.clear_status()
     oob = torch.tensor([1, 2, 5000], dtype=torch.int32, device="cuda")
