@@ -43,6 +43,8 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_INTERACTION = 38          # acceleration + jerk convention
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 METRIC = "pair-interactions/s (and % FP32 peak) at N=2^20, mixed vs FP64, at stated error"
+KERNEL_FILES = [os.path.join(ROOT, "paper_1411_5234_gb300", "csrc", f)
+                for f in ("nb_force_mixed.cuh", "nb_force_mixed.cu", "nb_internal.cuh")]
 UNIT = "pair-interactions/s"
 
 
@@ -57,12 +59,128 @@ def parse():
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="skip nb_autotune before timing")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--kernel-case", choices=["mixed", "fp64"], default=None,
                    help="run only nb_force on m random targets of N (profiling case)")
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--variant", type=int, default=None, help="mixed force kernel shape")
+    p.add_argument("--workload", default="step", choices=["step", "batch", "drift", "binaries"],
+                   help="step: the headline line; batch / drift / binaries: the other "
+                        "configurations (their own JSON lines)")
+    p.add_argument("--clusters", type=int, default=512)
+    p.add_argument("--t-end", type=float, default=None)
+    p.add_argument("--max-seconds", type=float, default=600.0,
+                   help="drift / binaries: wall-time bound of each integration")
+    p.add_argument("--fp64-n", type=int, default=None,
+                   help="binaries: N of the FP64 comparison run (default: the same N)")
     return p.parse_args()
+
+
+def integrate(sim, t_end, chunk=512, max_seconds=None):
+    """Block steps until every cluster reaches t_end, or until max_seconds of
+    wall time have passed; returns (device seconds, steps, time reached)."""
+    import torch
+    sim.set_end_time(sim.ticks(t_end))
+    target = sim.ticks(t_end)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    steps = 0
+    t_wall = time.perf_counter()
+    while True:
+        sim.step(chunk)
+        steps += chunk
+        st = sim.stats()
+        if st.t_min >= target:
+            break
+        if max_seconds is not None and time.perf_counter() - t_wall > max_seconds:
+            break
+    ev1.record(sim.stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) * 1e-3, steps, sim.time(st.t_min)
+
+
+def workload_batch(args):
+    """Independent Plummer clusters of log-uniform size in one context: every
+    block step advances every cluster; CUDA-graph-captured step sequences."""
+    import torch
+    from paper_1411_5234_gb300 import inputs, nbody
+    torch.cuda.set_device(0)
+    t_end = 0.25 if args.t_end is None else args.t_end
+    cl = inputs.plummer_batch(args.clusters, 256, 16384, seed0=0)
+    sizes = np.diff(cl.offsets)
+    kw = {} if args.variant is None else {"variant": args.variant}
+    out = {"workload": f"batch: {args.clusters} Plummer clusters, N_k log-uniform in [256, 16384] "
+                       f"(sum N = {cl.n}, sum N^2 = {float((sizes.astype(float) ** 2).sum()):.4g}), "
+                       f"seeds 0..{args.clusters - 1}, eps=1e-4, mixed, t = 0 -> {t_end}",
+           "metric": "pair-interactions/s over the run", "unit": UNIT}
+    # 1) the production run: graphs of 16 block steps
+    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, offsets=cl.offsets, eps=1e-4,
+                    precision=nbody.NB_MIXED, level_min=3, graph_steps=16, **kw)
+    e0 = np.add(*sim.energies())
+    secs, steps, _ = integrate(sim, t_end)
+    st = sim.stats()
+    e1 = np.add(*sim.energies())
+    drift = np.abs(e1 / e0 - 1)
+    assert sim.status() == nbody.NB_OK
+    out.update({"value": st.interactions / secs, "seconds": secs, "interactions": st.interactions,
+                "block_steps": st.block_steps,
+                "energy_drift": {"median": float(np.median(drift)), "max": float(drift.max())}})
+    sim.close()
+    # 2) the same run with force-kernel events (direct launches): its share
+    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, offsets=cl.offsets, eps=1e-4,
+                    precision=nbody.NB_MIXED, level_min=3, graph_steps=0, **kw)
+    sim.profile(True)
+    secs2, _, _ = integrate(sim, t_end)
+    fms, nlaunch = sim.profile_read()
+    out["force_kernel_share"] = fms * 1e-3 / secs2
+    out["nongraph_seconds"] = secs2
+    out["force_launches"] = nlaunch
+    sim.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def workload_drift(args):
+    """Energy drift over block steps, FP64 path vs mixed path, same initial conditions."""
+    import torch
+    from paper_1411_5234_gb300 import inputs, nbody
+    torch.cuda.set_device(0)
+    n = args.n if args.n != (1 << 20) else (262144 if args.workload == "binaries" else 65536)
+    t_end = 1.0 if args.t_end is None else args.t_end
+    if args.workload == "binaries":
+        cl = inputs.plummer_binaries(n, seed=0)
+        eps, lmax, label = 1e-5, 30, "Plummer with 10% binaries (a log-uniform 1e-4..1e-2, f(e)=2e)"
+    else:
+        cl = inputs.plummer(n, seed=0)
+        eps, lmax, label = 1e-4, 20, "Plummer equal mass"
+    out = {"workload": f"{label}, N={n}, eps={eps}, block steps 2^-3..2^-{lmax}, eta=0.01, "
+                       f"t = 0 -> {t_end}", "unit": UNIT}
+    runs = [("mixed", nbody.NB_MIXED, cl)]
+    if args.workload == "binaries" and args.fp64_n and args.fp64_n != n:
+        runs.append(("fp64", nbody.NB_FP64, inputs.plummer_binaries(args.fp64_n, seed=0)))
+        runs.append(("mixed_at_fp64_n", nbody.NB_MIXED, runs[-1][2]))
+    else:
+        runs.append(("fp64", nbody.NB_FP64, cl))
+    for name, prec, c in runs:
+        sim = nbody.Sim(c.pos, c.vel, c.mass, eps=eps, precision=prec, level_min=3,
+                        level_max=lmax, graph_steps=16)
+        e0 = sum(sim.energy())
+        secs, _, t_reached = integrate(sim, t_end, max_seconds=args.max_seconds)
+        e1 = sum(sim.energy())
+        st = sim.stats()
+        assert sim.status() == nbody.NB_OK
+        out[name] = {"N": c.n, "energy_drift": (e1 - e0) / abs(e0), "E0": e0,
+                     "t_reached": t_reached, "interactions": st.interactions,
+                     "block_steps": st.block_steps, "seconds": secs,
+                     "interactions_per_s": st.interactions / secs}
+        sim.close()
+    base = out.get("fp64", {}).get("energy_drift")
+    comp = out.get("mixed_at_fp64_n", out["mixed"])["energy_drift"]
+    if base:
+        out["mixed_over_fp64_drift"] = abs(comp) / abs(base)
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def kernel_case(args):
@@ -97,6 +215,23 @@ def kernel_case(args):
                       / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6)}), flush=True)
     sim.close()
     return 0
+
+
+def reduce_max(value, dist=None, device="cuda"):
+    """The maximum of a per-rank number over all ranks (the job's timed
+    region ends when its slowest rank ends); `value` itself on one rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput: every rank processed units_per_rank in at most
+    seconds_max (weak scaling: the per-rank work is fixed)."""
+    return world * units_per_rank / seconds_max
 
 
 def workload_config(n):
@@ -229,16 +364,22 @@ class ClockSampler:
                 "samples": len(self.rows), "reasons": reasons}
 
 
-def traffic_from_profile(kernel_file):
+def kernel_source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_files):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (same sha256), else None."""
+    the current kernel source (same sha256 of the kernel files), else None."""
     path = os.path.join(ROOT, "profiles", "force_mixed_n1048576.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    src = open(kernel_file, "rb").read()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    sha = kernel_source_sha(kernel_files)
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha256:\s*([0-9a-f]+)", text)
     if m and m.group(2) == sha:
         return float(m.group(1))
@@ -253,6 +394,10 @@ def main():
         return run_reference(args)
     if args.kernel_case:
         return kernel_case(args)
+    if args.workload == "batch":
+        return workload_batch(args)
+    if args.workload in ("drift", "binaries"):
+        return workload_drift(args)
 
     import torch
     from paper_1411_5234_gb300 import inputs, nbody
@@ -273,6 +418,10 @@ def main():
     sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nbody.NB_MIXED,
                     level_min=L, level_max=L, graph_steps=0, **kw)
     stream = sim.stream
+    tune = None
+    if not args.no_tune and args.variant is None:
+        variant, tms = sim.autotune()
+        tune = {"chosen_variant": variant, "ms_per_variant_at_fraction_1_1/16_1/256": tms}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     sim.profile(True)
 
@@ -307,22 +456,17 @@ def main():
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     force_ms, force_launches = sim.profile_read()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(step_ms), dist)
     assert sim.status() == nbody.NB_OK, nbody.strerror(sim.status())
     inter_step = n * n
-    value = world * args.steps * inter_step / (total_ms * 1e-3)
+    value = job_rate(args.steps * inter_step, world, total_ms * 1e-3)
     launches_per_step = 8   # tmin, predict, scan, scatter, plan, force, reduce, correct
 
     clocks = clk.summary()
     force_avg_s = force_ms * 1e-3 / max(force_launches, 1)
     achieved = FLOPS_PER_INTERACTION * inter_step / force_avg_s / 1e12
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    kfile = os.path.join(ROOT, "paper_1411_5234_gb300", "csrc", "nb_force_mixed.cu")
-    traffic = traffic_from_profile(kfile)
+    traffic = traffic_from_profile(KERNEL_FILES)
     roofline = {"bound": "alu", "kernel": "k_force_mixed", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "flops_per_interaction": FLOPS_PER_INTERACTION,
@@ -335,6 +479,8 @@ def main():
         roofline["frac_at_sampled_clock"] = achieved / pk
 
     roofline["kernel_shape_variant"] = sim.cfg.variant
+    if tune:
+        roofline["autotune"] = tune
     wt, nt = sim.tile_stats()
     roofline["near_tile_share"] = nt / max(wt, 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -360,13 +506,9 @@ def main():
             sim.get_state_into(hp, hv, ha, hj, ht, hl)
             if k >= args.warmup:
                 e2e_t.append(time.perf_counter() - t0)
-        tot = sum(e2e_t)
-        if dist:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = reduce_max(sum(e2e_t), dist)
         h2d = 4 * 24 * n + 8 * n + 4 * n
-        line["e2e"] = {"value": world * args.steps * inter_step / tot, "unit": UNIT,
+        line["e2e"] = {"value": job_rate(args.steps * inter_step, world, tot), "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                        "api": "nb_set_state + nb_step_block + nb_get_state (pinned host)"}
     sim.close()

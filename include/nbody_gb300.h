@@ -90,8 +90,8 @@ typedef struct {
     int32_t sort_sources;/* 1: force sources kept in spatial (Hilbert) order of
                             the initial positions, 0: in particle order.  Only
                             speed depends on it, never the results' accuracy. */
-    int32_t variant;    /* shape of the mixed force kernel, 0..3 (see
-                           nb_force_mixed.cu); all give results of the same
+    int32_t variant;    /* shape of the mixed force kernel, 0 .. NB_MIXED_VARIANTS-1
+                           (see nb_autotune); all give results of the same
                            accuracy */
 } nb_config;
 
@@ -166,6 +166,11 @@ int nb_set_end_time(nb_ctx *ctx, int64_t t_end_ticks);
  * block time.  Host outputs; synchronises. */
 int nb_energy(nb_ctx *ctx, int32_t cluster, double *ekin, double *epot);
 
+/* The same energies for every cluster from ONE potential evaluation of the
+ * whole context: ekin[k], epot[k] for k < n_clusters (host arrays).
+ * Synchronises. */
+int nb_energies(nb_ctx *ctx, double *ekin, double *epot);
+
 /* Copy the state to host arrays (any pointer may be NULL): pos, vel, acc,
  * jerk (n x 3), t (n ticks), level (n).  The vectors are packed on the device
  * and copied straight into the caller's arrays (pinned arrays copy at full
@@ -200,6 +205,19 @@ int nb_profile_read(nb_ctx *ctx, double *force_ms, int64_t *launches);
  * 2.5 tile radii.  The near share measures how well the spatial source order
  * fits the targets; it affects speed only.  Synchronises. */
 int nb_tile_stats(nb_ctx *ctx, int64_t *warp_tiles, int64_t *near_warp_tiles);
+
+/* Autotuner: time every compiled shape of the mixed force kernel (see
+ * nb_config.variant) on this context's own sources, for targets taken every
+ * 1st, 16th and 256th source slot (the active fractions a block step sees),
+ * and keep the shape with the least total time for the context's later
+ * nb_force and nb_step_block calls.  variant_out (host, may be NULL) gets
+ * the choice; ms_out (host, NB_TUNE_POINTS x variants doubles, may be NULL)
+ * gets the timings [variant][fraction].  Uses the workspace's active-list
+ * buffers (call it between steps); FP64 contexts return their shape.
+ * Synchronises. */
+#define NB_TUNE_POINTS 3
+#define NB_MIXED_VARIANTS 6
+int nb_autotune(nb_ctx *ctx, int32_t *variant_out, double *ms_out);
 
 /* Sticky device status (NB_OK or an NB_E* code); synchronises. */
 int nb_status(nb_ctx *ctx);

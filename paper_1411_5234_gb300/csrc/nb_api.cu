@@ -184,6 +184,7 @@ struct nb_ctx {
   int grid_mix = 0, grid_f64 = 0;
   std::vector<int64_t> off_host;
   std::vector<double> mass_host;
+  std::vector<int32_t> sperm_host;  // source slot order (for the autotuner's target lists)
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
   bool graph_broken = false;
@@ -494,6 +495,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   }
   std::vector<int32_t> sperm(S), sinv(N);
   source_order(pos, offsets, n_clusters, soff.data(), cfg->sort_sources != 0, sperm, sinv);
+  c->sperm_host = sperm;
   for (int64_t i = 0; i < N; ++i) {
     p4[4 * i] = pos[3 * i];
     p4[4 * i + 1] = pos[3 * i + 1];
@@ -662,6 +664,31 @@ int nb_energy(nb_ctx* c, int32_t cluster, double* ekin, double* epot) {
   return NB_OK;
 }
 
+int nb_energies(nb_ctx* c, double* ekin, double* epot) {
+  if (!c || !ekin || !epot) return NB_EINVAL;
+  Dev& d = c->d;
+  double* an = reinterpret_cast<double*>(d.acc_new);
+  NB_TRY(launch_predict(d, d.t_cur, 0, c->cfg.tick_exp, false, true, false, c->st));
+  NB_TRY(launch_actoff_identity(d, c->st));
+  NB_TRY(enqueue_force(c, nullptr, nullptr, nullptr, 0, nullptr, 0, an + 3, 4, true, 0, 0, true,
+                       d.N));
+  std::vector<double> h(2 * (size_t)d.K);
+  double* out = d.esum + 2 * kEnergyBlocks;
+  for (int32_t k = 0; k < d.K; ++k) {
+    NB_TRY(launch_energy(d, an + 3, 4, c->off_host[k], c->off_host[k + 1], d.esum, kEnergyBlocks,
+                         out, c->st));
+    NB_TRY(cudaMemcpyAsync(h.data() + 2 * k, out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->st));
+  }
+  const int rc = sync_status(c);
+  if (rc != NB_OK) return rc;
+  for (int32_t k = 0; k < d.K; ++k) {
+    ekin[k] = h[2 * k];
+    epot[k] = h[2 * k + 1];
+  }
+  return NB_OK;
+}
+
 int nb_get_state(nb_ctx* c, double* pos, double* vel, double* acc, double* jerk, int64_t* t,
                  int32_t* level) {
   if (!c) return NB_EINVAL;
@@ -762,6 +789,94 @@ int nb_tile_stats(nb_ctx* c, int64_t* warp_tiles, int64_t* near_warp_tiles) {
   if (warp_tiles) *warp_tiles = (int64_t)ctr[0];
   if (near_warp_tiles) *near_warp_tiles = (int64_t)ctr[1];
   return NB_OK;
+}
+
+int nb_autotune(nb_ctx* c, int32_t* variant_out, double* ms_out) {
+  if (!c) return NB_EINVAL;
+  if (c->cfg.precision != NB_MIXED) {  // one FP64 shape: nothing to choose
+    if (variant_out) *variant_out = c->cfg.variant;
+    return NB_OK;
+  }
+  Dev& d = c->d;
+  const int nv = force_mixed_variants();
+  const int fracs[3] = {1, 16, 256};
+  std::vector<double> ms(static_cast<size_t>(nv) * 3, 0.0);
+  cudaEvent_t e0, e1;
+  NB_TRY(cudaEventCreate(&e0));
+  NB_TRY(cudaEventCreate(&e1));
+  const int saved = c->cfg.variant;
+  int rc = NB_OK;
+  double* an = reinterpret_cast<double*>(d.acc_new);
+  double* jn = reinterpret_cast<double*>(d.jerk_new);
+  for (int fi = 0; fi < 3 && rc == NB_OK; ++fi) {
+    // every fracs[fi]-th source slot of each cluster, in slot order
+    std::vector<int32_t> list;
+    std::vector<int32_t> aoff(d.K + 1, 0);
+    std::vector<int64_t> soff(d.K + 1, 0);
+    for (int32_t k = 0; k < d.K; ++k)
+      soff[k + 1] = soff[k] + round_up64(c->off_host[k + 1] - c->off_host[k], 4);
+    for (int32_t k = 0; k < d.K; ++k) {
+      aoff[k] = static_cast<int32_t>(list.size());
+      for (int64_t sl = soff[k]; sl < soff[k + 1]; sl += fracs[fi])
+        if (c->sperm_host[sl] >= 0) list.push_back(c->sperm_host[sl]);
+    }
+    aoff[d.K] = static_cast<int32_t>(list.size());
+    if (list.empty()) continue;
+    if (cudaMemcpyAsync(d.active, list.data(), 4 * list.size(), cudaMemcpyHostToDevice, c->st) ||
+        cudaMemcpyAsync(d.act_off, aoff.data(), 4 * aoff.size(), cudaMemcpyHostToDevice, c->st) ||
+        cudaStreamSynchronize(c->st)) {
+      rc = NB_ECUDA;
+      break;
+    }
+    for (int v = 0; v < nv && rc == NB_OK; ++v) {
+      c->cfg.variant = v;
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      c->grid_mix = sms * force_mixed_ctas_per_sm(v);
+      float best = 1e30f;
+      for (int r = 0; r < 3; ++r) {  // one warm-up, best of two
+        if (cudaEventRecord(e0, c->st) ||
+            enqueue_force(c, d.active, nullptr, an, 4, jn, 4, nullptr, 0, false, 0, 0, false,
+                          d.N) ||
+            cudaEventRecord(e1, c->st) || cudaEventSynchronize(e1)) {
+          rc = NB_ECUDA;
+          break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0 && t < best) best = t;
+      }
+      ms[static_cast<size_t>(v) * 3 + fi] = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int choice = saved;
+  if (rc == NB_OK) {
+    double best = 1e300;
+    for (int v = 0; v < nv; ++v) {
+      const double tot = ms[v * 3] + ms[v * 3 + 1] + ms[v * 3 + 2];
+      if (tot < best) {
+        best = tot;
+        choice = v;
+      }
+    }
+  }
+  c->cfg.variant = choice;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  c->grid_mix = sms * force_mixed_ctas_per_sm(choice);
+  if (c->graph) {  // captured with the previous shape
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (variant_out) *variant_out = choice;
+  if (ms_out)
+    for (size_t q = 0; q < ms.size(); ++q) ms_out[q] = ms[q];
+  if (rc != NB_OK) return rc;
+  return sync_status(c);
 }
 
 int nb_status(nb_ctx* c) {

@@ -7,6 +7,9 @@
 //   1: 128 threads x 2 targets, totals in registers, 1/s^2 from the SFU
 //   2:  64 threads x 4 targets, totals in shared memory, 1/s^2 = rsqrt^2
 //   3: 256 threads x 1 target,  totals in registers, 1/s^2 from the SFU
+//   4:  64 threads x 3 targets, totals in shared memory, 1/s^2 = rsqrt^2
+//   5:  32 threads x 4 targets (one warp per CTA), shared-memory totals
+#include "../../include/nbody_gb300.h"
 #include "nb_force_mixed.cuh"
 
 namespace nb {
@@ -15,6 +18,8 @@ template <bool POT> using S0 = mixk::MixShape<128, 2, POT, false, false, 2, 2>;
 template <bool POT> using S1 = mixk::MixShape<128, 2, POT, true, false, 2, 2>;
 template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 2, 4>;
 template <bool POT> using S3 = mixk::MixShape<256, 1, POT, true, false, 4, 2>;
+template <bool POT> using S4 = mixk::MixShape<64, 3, POT, false, true, 2, 5>;
+template <bool POT> using S5 = mixk::MixShape<32, 4, POT, false, true, 2, 8>;
 
 template <class Sh>
 cudaError_t launch_shape(const ForceArgs& a, int grid, cudaStream_t st) {
@@ -37,13 +42,15 @@ int occupancy_both() {
 }
 }  // namespace
 
-int force_mixed_variants() { return 4; }
+int force_mixed_variants() { return NB_MIXED_VARIANTS; }
 
 int force_mixed_ni(int variant) {
   switch (variant) {
     case 1: return S1<false>::NI;
     case 2: return S2<false>::NI;
     case 3: return S3<false>::NI;
+    case 4: return S4<false>::NI;
+    case 5: return S5<false>::NI;
     default: return S0<false>::NI;
   }
 }
@@ -54,6 +61,8 @@ cudaError_t launch_force_mixed(const ForceArgs& a, int grid, bool with_pot, int 
     case 1: return with_pot ? launch_shape<S1<true>>(a, grid, st) : launch_shape<S1<false>>(a, grid, st);
     case 2: return with_pot ? launch_shape<S2<true>>(a, grid, st) : launch_shape<S2<false>>(a, grid, st);
     case 3: return with_pot ? launch_shape<S3<true>>(a, grid, st) : launch_shape<S3<false>>(a, grid, st);
+    case 4: return with_pot ? launch_shape<S4<true>>(a, grid, st) : launch_shape<S4<false>>(a, grid, st);
+    case 5: return with_pot ? launch_shape<S5<true>>(a, grid, st) : launch_shape<S5<false>>(a, grid, st);
     default: return with_pot ? launch_shape<S0<true>>(a, grid, st) : launch_shape<S0<false>>(a, grid, st);
   }
 }
@@ -63,6 +72,8 @@ int force_mixed_ctas_per_sm(int variant) {
     case 1: return occupancy_both<S1>();
     case 2: return occupancy_both<S2>();
     case 3: return occupancy_both<S3>();
+    case 4: return occupancy_both<S4>();
+    case 5: return occupancy_both<S5>();
     default: return occupancy_both<S0>();
   }
 }

@@ -227,11 +227,16 @@ __global__ void k_plan(Dev d, PlanArgs p) {
       } else {
         // fill the persistent grid, then pick the split whose last round of
         // work items is fullest
-        const int64_t b0 = max((int64_t)1, ceil_div64(p.grid, (int64_t)nit));
+        // a few candidates above the fill point, 32-bit arithmetic (the
+        // per-cluster clamp below bounds B by the cluster's tile count anyway)
+        const uint32_t g = static_cast<uint32_t>(p.grid);
+        const uint32_t n = nit > (1ull << 30) ? (1u << 30) : static_cast<uint32_t>(nit);
+        const uint32_t b0 = n >= g ? 1u : (g + n - 1) / n;
         double best = -1.0;
-        for (int64_t b = b0; b <= 2 * b0 + 2; ++b) {
-          const int64_t items = (int64_t)nit * b;
-          const double eff = (double)items / (double)(ceil_div64(items, p.grid) * p.grid);
+        for (uint32_t b = b0; b <= b0 + 8; ++b) {
+          const uint64_t items = (uint64_t)n * b;
+          const uint64_t rounds = (items + g - 1) / g;
+          const double eff = (double)items / (double)(rounds * g);
           if (eff > best + 1e-3) { best = eff; bg = b; }
         }
       }
@@ -272,30 +277,39 @@ __global__ void k_plan(Dev d, PlanArgs p) {
   if (threadIdx.x == 0) d.item_off[K] = carry;
 }
 
-// Fixed-order sum of the B_k partials of every target whose cluster was split.
+// Fixed-order sum of the B_k partials of every target whose cluster was
+// split: one warp per target, lane l sums partials b = l, l + 32, ... in
+// order, then a fixed butterfly combines the lanes (deterministic).
 __global__ void k_reduce(ForceArgs a, int NI, int with_acc) {
   const int32_t m = a.act_off[a.K];
-  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int32_t wpb = blockDim.x >> 5;
+  for (int32_t s = blockIdx.x * wpb + (threadIdx.x >> 5); s < m; s += gridDim.x * wpb) {
     const int32_t k = upper_bound_i32(a.act_off, a.K + 1, s) - 1;
     const int32_t B = a.bfac[k];
-    if (B <= 1) continue;
+    if (B <= 1) continue;  // uniform over the warp
     const int32_t local = s - a.act_off[k];
     const int32_t it = local / NI, q = local - it * NI;
     const int32_t w0 = a.item_off[k] + it * B;
     double v[kPartialComps];
 #pragma unroll
     for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
-    for (int32_t b = 0; b < B; ++b) {
+    for (int32_t b = lane; b < B; b += 32) {
       const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
 #pragma unroll
       for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
     }
-    const int64_t row = a.rows ? (int64_t)a.rows[s] : (int64_t)s;
-    if (with_acc) {
-      if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[row * a.sa + c] = a.G * v[c];
-      if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[row * a.sj + c] = a.G * v[3 + c];
+#pragma unroll
+    for (int c = 0; c < kPartialComps; ++c)
+      for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    if (lane == 0) {
+      const int64_t row = a.rows ? (int64_t)a.rows[s] : (int64_t)s;
+      if (with_acc) {
+        if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[row * a.sa + c] = a.G * v[c];
+        if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[row * a.sj + c] = a.G * v[3 + c];
+      }
+      if (a.out_pot) a.out_pot[row * a.sp] = a.G * v[6];
     }
-    if (a.out_pot) a.out_pot[row * a.sp] = a.G * v[6];
   }
 }
 
@@ -360,15 +374,19 @@ __global__ void k_correct(Dev d, CorrectArgs c) {
     const double j1[3] = {c.jerk[s * c.sj], c.jerk[s * c.sj + 1], c.jerk[s * c.sj + 2]};
     const double a0v[3] = {a0.x, a0.y, a0.z}, j0v[3] = {j0.x, j0.y, j0.z};
     const double xpv[3] = {xp.x, xp.y, xp.z}, vpv[3] = {vp.x, vp.y, vp.z};
+    // the Hermite fit's divisions as multiplications by 1/t^2, 1/t^3 and
+    // the Taylor coefficients (FP64 division is a long sequence here)
     const double t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
+    const double it2 = 1.0 / t2, it3 = it2 / t;
+    const double c24 = t4 * (1.0 / 24.0), c120 = t5 * (1.0 / 120.0), c6 = t3 * (1.0 / 6.0);
     double x1[3], v1[3], a2e[3], a3[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const double da = a0v[q] - a1[q];
-      const double a2 = (-6.0 * da - t * (4.0 * j0v[q] + 2.0 * j1[q])) / t2;
-      a3[q] = (12.0 * da + 6.0 * t * (j0v[q] + j1[q])) / t3;
-      x1[q] = xpv[q] + a2 * t4 / 24.0 + a3[q] * t5 / 120.0;
-      v1[q] = vpv[q] + a2 * t3 / 6.0 + a3[q] * t4 / 24.0;
+      const double a2 = (-6.0 * da - t * (4.0 * j0v[q] + 2.0 * j1[q])) * it2;
+      a3[q] = (12.0 * da + 6.0 * t * (j0v[q] + j1[q])) * it3;
+      x1[q] = xpv[q] + a2 * c24 + a3[q] * c120;
+      v1[q] = vpv[q] + a2 * c6 + a3[q] * c24;
       a2e[q] = a2 + a3[q] * t;
     }
     const double dt = aarseth(norm3(a1[0], a1[1], a1[2]), norm3(j1[0], j1[1], j1[2]),
@@ -553,7 +571,8 @@ cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
 }
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
                           cudaStream_t st) {
-  k_reduce<<<blocks_for(m_bound, 256), 256, 0, st>>>(a, NI, with_acc ? 1 : 0);
+  // one warp per target: 8 targets per CTA of 256 threads
+  k_reduce<<<blocks_for(m_bound, 8), 256, 0, st>>>(a, NI, with_acc ? 1 : 0);
   return cudaGetLastError();
 }
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {

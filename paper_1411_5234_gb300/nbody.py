@@ -18,12 +18,14 @@ from . import build as _build
 
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ETIMEOUT, NB_ENONFINITE, NB_ESTATE = range(7)
 NB_FP64, NB_MIXED = 0, 1
+MIXED_VARIANTS = 6    # NB_MIXED_VARIANTS: shapes of the mixed force kernel
 
 FUNCTIONS = [
     "nb_default_config", "nb_workspace_size", "nb_init", "nb_free", "nb_predict", "nb_force",
     "nb_correct", "nb_step_block", "nb_set_end_time", "nb_energy", "nb_get_state",
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
     "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
+    "nb_energies", "nb_autotune",
 ]
 
 
@@ -73,6 +75,8 @@ def _load() -> ctypes.CDLL:
         "nb_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "nb_profile_read": (ctypes.c_int, [P, P, P]),
         "nb_tile_stats": (ctypes.c_int, [P, P, P]),
+        "nb_energies": (ctypes.c_int, [P, P, P]),
+        "nb_autotune": (ctypes.c_int, [P, P, P]),
         "nb_force_noalloc": (ctypes.c_int, [P, P, P, i64, P, i64, ctypes.c_double,
                                             ctypes.c_double, i32, P, P, P, P]),
     }
@@ -229,6 +233,22 @@ class Sim:
         _check(lib.nb_energy(self._ctx, int(cluster), ctypes.byref(ek), ctypes.byref(ep)),
                "nb_energy")
         return ek.value, ep.value
+
+    def energies(self):
+        """(ekin[K], epot[K]) of every cluster from one potential evaluation."""
+        ek = np.empty(self.n_clusters)
+        ep = np.empty(self.n_clusters)
+        _check(lib.nb_energies(self._ctx, _hptr(ek), _hptr(ep)), "nb_energies")
+        return ek, ep
+
+    def autotune(self):
+        """Pick the fastest mixed kernel shape for this context; returns
+        (variant, {variant: [ms at fraction 1, 1/16, 1/256]})."""
+        v = ctypes.c_int32()
+        ms = np.zeros(3 * MIXED_VARIANTS)
+        _check(lib.nb_autotune(self._ctx, ctypes.byref(v), _hptr(ms)), "nb_autotune")
+        self.cfg.variant = v.value
+        return v.value, {k: ms[3 * k:3 * k + 3].tolist() for k in range(MIXED_VARIANTS)}
 
     def get_state(self):
         n = self.n

@@ -352,6 +352,9 @@ def test_energy_matches_oracle(nb):
         tot[1] += rp
     ek, ep = sim.energy(-1)
     assert ek == pytest.approx(tot[0], rel=1e-13) and ep == pytest.approx(tot[1], rel=1e-12)
+    eks, eps_ = sim.energies()                    # all clusters from one evaluation
+    for k in range(3):
+        assert (eks[k], eps_[k]) == sim.energy(k)
     sim.close()
 
 
@@ -377,4 +380,24 @@ def test_invalid_arguments(nb):
     a = torch.zeros((2, 3), dtype=torch.float64, device="cuda")
     sim.correct(0, act, a, a)
     assert sim.status() == nb.NB_EINVAL
+    sim.close()
+
+
+def test_autotune_picks_a_shape_and_keeps_results(nb):
+    cl = inputs.plummer(6000, seed=41, imf="kroupa")
+    idx = inputs.random_active(6000, 1500, seed=2)
+    act = torch.as_tensor(idx, device="cuda")
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nb.NB_MIXED, graph_steps=4)
+    sim.predict(0)
+    a0, j0, _ = (x.cpu().numpy() for x in sim.force(act))
+    v, ms = sim.autotune()
+    assert 0 <= v < nb.MIXED_VARIANTS and all(t > 0 for row in ms.values() for t in row)
+    sim.predict(0)
+    a1, j1, _ = (x.cpu().numpy() for x in sim.force(act))
+    ra, rj, _ = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx)
+    Sa, Sj = term_sums(cl, 1e-4, idx)
+    check_mixed(a1, j1, ra, rj, Sa, Sj)
+    check_mixed(a0, j0, ra, rj, Sa, Sj)
+    sim.step(9)                                   # graphs rebuilt with the chosen shape
+    assert sim.status() == nb.NB_OK
     sim.close()

@@ -1,0 +1,60 @@
+"""The multi-rank benchmark path on CPU: two gloo ranks, no GPU.
+
+Under torchrun every rank integrates its own independent cluster (seed =
+rank) with no data-path collective; the only cross-rank operations are the
+barrier around the timed region and the all-reduce MAX of its duration.
+These tests run exactly those operations of bench.py on world size 2.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    from paper_1411_5234_gb300 import inputs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.barrier()
+    local_ms = 100.0 + 50.0 * rank                 # rank 1 is the slow one
+    worst = bench.reduce_max(local_ms, dist, device="cpu")
+    value = bench.job_rate(3 * 1024 * 1024, world, worst * 1e-3)
+    cl = bench.make_cluster(512, seed=rank)        # the rank's own cluster
+    np.save(os.path.join(out_dir, f"r{rank}.npy"),
+            np.array([worst, value, cl.pos[0, 0], cl.mass.sum()]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_only_the_timing():
+    torch = pytest.importorskip("torch")
+    import tempfile
+    import torch.multiprocessing as mp
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_rank_main, args=(2, _free_port(), d), nprocs=2, join=True,
+                           start_method="spawn")
+        r0, r1 = (np.load(os.path.join(d, f"r{k}.npy")) for k in (0, 1))
+    assert r0[0] == r1[0] == 150.0                  # max over ranks
+    assert r0[1] == r1[1] == pytest.approx(2 * 3 * 1024 * 1024 / 0.150)
+    assert r0[2] != r1[2]                           # independent clusters per rank
+    assert r0[3] == pytest.approx(1.0) and r1[3] == pytest.approx(1.0)
+
+
+def test_single_rank_helpers():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max(42.0) == 42.0
+    assert bench.job_rate(10, 4, 2.0) == 20.0
