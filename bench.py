@@ -117,6 +117,9 @@ def workload_batch(args):
     # 1) the production run: graphs of 16 block steps
     sim = nbody.Sim(cl.pos, cl.vel, cl.mass, offsets=cl.offsets, eps=1e-4,
                     precision=nbody.NB_MIXED, level_min=3, graph_steps=16, **kw)
+    if args.variant is None and not args.no_tune:
+        kw = {"variant": sim.autotune()[0]}
+        out["autotuned_variant"] = kw["variant"]
     e0 = np.add(*sim.energies())
     secs, steps, _ = integrate(sim, t_end)
     st = sim.stats()
@@ -147,7 +150,7 @@ def workload_drift(args):
     from paper_1411_5234_gb300 import inputs, nbody
     torch.cuda.set_device(0)
     n = args.n if args.n != (1 << 20) else (262144 if args.workload == "binaries" else 65536)
-    t_end = 1.0 if args.t_end is None else args.t_end
+    t_end = (0.125 if args.workload == "binaries" else 1.0) if args.t_end is None else args.t_end
     if args.workload == "binaries":
         cl = inputs.plummer_binaries(n, seed=0)
         eps, lmax, label = 1e-5, 30, "Plummer with 10% binaries (a log-uniform 1e-4..1e-2, f(e)=2e)"
@@ -165,6 +168,8 @@ def workload_drift(args):
     for name, prec, c in runs:
         sim = nbody.Sim(c.pos, c.vel, c.mass, eps=eps, precision=prec, level_min=3,
                         level_max=lmax, graph_steps=16)
+        if prec == nbody.NB_MIXED and not args.no_tune:
+            sim.autotune()
         e0 = sum(sim.energy())
         secs, _, t_reached = integrate(sim, t_end, max_seconds=args.max_seconds)
         e1 = sum(sim.energy())

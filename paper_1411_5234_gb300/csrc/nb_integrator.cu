@@ -278,37 +278,68 @@ __global__ void k_plan(Dev d, PlanArgs p) {
 }
 
 // Fixed-order sum of the B_k partials of every target whose cluster was
-// split: one warp per target, lane l sums partials b = l, l + 32, ... in
-// order, then a fixed butterfly combines the lanes (deterministic).
+// split.  Each lane owns one target of its warp's 32 consecutive targets:
+// with B_k <= kReduceSerial the lane sums b = 0 .. B_k - 1 in order; larger
+// B_k are taken one target at a time by the whole warp (lane l sums
+// b = l, l + 32, ... in order, then a fixed butterfly).  Deterministic.
+constexpr int kReduceSerial = 16;
+
+__device__ __forceinline__ void write_reduced(const ForceArgs& a, int32_t s, const double* v,
+                                              int with_acc) {
+  const int64_t row = a.rows ? (int64_t)a.rows[s] : (int64_t)s;
+  if (with_acc) {
+    if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[row * a.sa + c] = a.G * v[c];
+    if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[row * a.sj + c] = a.G * v[3 + c];
+  }
+  if (a.out_pot) a.out_pot[row * a.sp] = a.G * v[6];
+}
+
 __global__ void k_reduce(ForceArgs a, int NI, int with_acc) {
   const int32_t m = a.act_off[a.K];
   const int lane = threadIdx.x & 31;
-  const int32_t wpb = blockDim.x >> 5;
-  for (int32_t s = blockIdx.x * wpb + (threadIdx.x >> 5); s < m; s += gridDim.x * wpb) {
-    const int32_t k = upper_bound_i32(a.act_off, a.K + 1, s) - 1;
-    const int32_t B = a.bfac[k];
-    if (B <= 1) continue;  // uniform over the warp
-    const int32_t local = s - a.act_off[k];
-    const int32_t it = local / NI, q = local - it * NI;
-    const int32_t w0 = a.item_off[k] + it * B;
-    double v[kPartialComps];
-#pragma unroll
-    for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
-    for (int32_t b = lane; b < B; b += 32) {
-      const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
-#pragma unroll
-      for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
+  const int32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int32_t s0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; s0 < m;
+       s0 += nwarps * 32) {
+    const int32_t s = s0 + lane;
+    int32_t B = 0, w0 = 0, q = 0;
+    if (s < m) {
+      const int32_t k = upper_bound_i32(a.act_off, a.K + 1, s) - 1;
+      B = a.bfac[k];
+      const int32_t local = s - a.act_off[k];
+      const int32_t it = local / NI;
+      q = local - it * NI;
+      w0 = a.item_off[k] + it * B;
     }
+    if (B > 1 && B <= kReduceSerial) {
+      double v[kPartialComps];
 #pragma unroll
-    for (int c = 0; c < kPartialComps; ++c)
-      for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-    if (lane == 0) {
-      const int64_t row = a.rows ? (int64_t)a.rows[s] : (int64_t)s;
-      if (with_acc) {
-        if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[row * a.sa + c] = a.G * v[c];
-        if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[row * a.sj + c] = a.G * v[3 + c];
+      for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
+      for (int32_t b = 0; b < B; ++b) {
+        const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
+#pragma unroll
+        for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
       }
-      if (a.out_pot) a.out_pot[row * a.sp] = a.G * v[6];
+      write_reduced(a, s, v, with_acc);
+    }
+    unsigned big = __ballot_sync(0xffffffffu, B > kReduceSerial);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const int32_t Bs = __shfl_sync(0xffffffffu, B, src);
+      const int32_t w0s = __shfl_sync(0xffffffffu, w0, src);
+      const int32_t qs = __shfl_sync(0xffffffffu, q, src);
+      double v[kPartialComps];
+#pragma unroll
+      for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
+      for (int32_t b = lane; b < Bs; b += 32) {
+        const double* P = a.partials + (size_t)(w0s + b) * kPartialComps * NI + qs;
+#pragma unroll
+        for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
+      }
+#pragma unroll
+      for (int c = 0; c < kPartialComps; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+      if (lane == 0) write_reduced(a, s0 + src, v, with_acc);
     }
   }
 }
@@ -571,8 +602,8 @@ cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
 }
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
                           cudaStream_t st) {
-  // one warp per target: 8 targets per CTA of 256 threads
-  k_reduce<<<blocks_for(m_bound, 8), 256, 0, st>>>(a, NI, with_acc ? 1 : 0);
+  // one lane per target, warps of 32 consecutive targets
+  k_reduce<<<blocks_for(m_bound, 256), 256, 0, st>>>(a, NI, with_acc ? 1 : 0);
   return cudaGetLastError();
 }
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {
