@@ -16,7 +16,8 @@ Reported (one JSON line from rank 0):
   roofline   the mixed force kernel at 38 flops per interaction against the
              FP32 peak 152 SMs x 128 lanes x 2 flops x 2.070 GHz;
   sweep      nb_force alone at active fractions 2^-10 .. 1 (mixed) and
-             2^-10 .. 2^-6 (FP64), with error vs FP64 and vs the oracle;
+             2^-10 .. 2^-6 (FP64), with the mixed path's error vs the FP64
+             path (the oracle checks both paths in tests/);
   cpu_baseline  the FP64 CPU oracle on the host cores, on a sample of targets.
 Multi-GPU (torchrun): every rank integrates its own independent cluster
 (seed = rank), no data-path collective; value sums the ranks' interactions.
@@ -204,6 +205,7 @@ def kernel_case(args):
     for _ in range(args.warmup):
         sim.force(act, acc, jerk, None, want_pot=False)
     sim.synchronize()
+    wt0, nt0 = sim.tile_stats()
     sim.profile(True)
     for _ in range(args.steps):
         sim.force(act, acc, jerk, None, want_pot=False)
@@ -213,7 +215,7 @@ def kernel_case(args):
     rate = args.m * cl.n / (per * 1e-3)
     wt, nt = sim.tile_stats()
     print(json.dumps({"kernel_case": args.kernel_case, "variant": sim.cfg.variant,
-                      "near_tile_share": nt / max(wt, 1),
+                      "near_tile_share": (nt - nt0) / max(wt - wt0, 1),
                       "N": cl.n, "m": args.m,
                       "ms_per_launch": per, "interactions_per_s": rate,
                       "frac_fp32_peak_38": FLOPS_PER_INTERACTION * rate
@@ -444,6 +446,7 @@ def main():
         one_step()
     stream.synchronize()
     sim.profile_read()                      # drop warm-up launches
+    wt0, nt0 = sim.tile_stats()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -487,7 +490,7 @@ def main():
     if tune:
         roofline["autotune"] = tune
     wt, nt = sim.tile_stats()
-    roofline["near_tile_share"] = nt / max(wt, 1)
+    roofline["near_tile_share"] = (nt - nt0) / max(wt - wt0, 1)   # timed steps only
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -563,8 +566,8 @@ def sweep(nbody, inputs, torch, cl):
                 entry["frac_fp32_peak"] = (FLOPS_PER_INTERACTION * rate
                                            / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6))
             out[name].append(entry)
-    # accuracy: mixed vs FP64 on 4096 targets; both vs the oracle on 64 targets
-    import oracle
+    # accuracy: mixed vs FP64 on 4096 targets (GPU against GPU; the oracle
+    # checks both paths at this size in tests/test_gpu_full_size.py)
     idx = inputs.random_active(n, 4096, seed=123)
     act = torch.as_tensor(idx, device="cuda")
     res = {}
@@ -575,20 +578,12 @@ def sweep(nbody, inputs, torch, cl):
     rel = lambda x, r: np.linalg.norm(x - r, axis=1) / np.linalg.norm(r, axis=1)
     ea, ej = rel(res["mixed"][0], res["fp64"][0]), rel(res["mixed"][1], res["fp64"][1])
     ep = np.abs(res["mixed"][2] / res["fp64"][2] - 1)
-    sub = np.arange(0, 4096, 64)
-    ra, rj, _ = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx[sub].astype(np.int64))
     out["accuracy"] = {
         "mixed_vs_fp64_4096_targets": {
             "acc_rel_max": float(ea.max()), "acc_rel_median": float(np.median(ea)),
             "acc_rel_p999": float(np.quantile(ea, 0.999)),
             "jerk_rel_max": float(ej.max()), "jerk_rel_median": float(np.median(ej)),
-            "pot_rel_max": float(ep.max())},
-        "fp64_vs_oracle_64_targets": {
-            "acc_rel_max": float(rel(res["fp64"][0][sub], ra).max()),
-            "jerk_rel_max": float(rel(res["fp64"][1][sub], rj).max())},
-        "mixed_vs_oracle_64_targets": {
-            "acc_rel_max": float(rel(res["mixed"][0][sub], ra).max()),
-            "jerk_rel_max": float(rel(res["mixed"][1][sub], rj).max())}}
+            "pot_rel_max": float(ep.max())}}
     mx = {e["m"]: e["interactions_per_s"] for e in out["mixed"]}
     out["mixed_over_fp64_speedup"] = {e["active_fraction"]: mx[e["m"]] / e["interactions_per_s"]
                                       for e in out["fp64"]}

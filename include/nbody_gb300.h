@@ -200,10 +200,13 @@ int nb_profile_enable(nb_ctx *ctx, int enable);
 int nb_profile_read(nb_ctx *ctx, double *force_ms, int64_t *launches);
 
 /* Mixed force kernel diagnostics since nb_init (host outputs, either may be
- * NULL): source tiles processed by a warp, and how many of those took the
- * near (full double-single) path because some target of the warp lay within
- * 2.5 tile radii.  The near share measures how well the spatial source order
- * fits the targets; it affects speed only.  Synchronises. */
+ * NULL): source cells (64 slots each) processed by a warp, and how many of
+ * those took the near (full double-single) path because some target of the
+ * warp lay within 2 cell radii of the cell centre.  The near share measures
+ * how well the spatial source order fits the targets; it affects speed only.
+ * The counts accumulate over every mixed launch of the context (nb_init's
+ * own force evaluation included); take differences to cover a span.
+ * Synchronises. */
 int nb_tile_stats(nb_ctx *ctx, int64_t *warp_tiles, int64_t *near_warp_tiles);
 
 /* Autotuner: time every compiled shape of the mixed force kernel (see

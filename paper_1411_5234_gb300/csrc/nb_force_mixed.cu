@@ -16,10 +16,10 @@ namespace nb {
 namespace {
 template <bool POT> using S0 = mixk::MixShape<128, 2, POT, false, false, 2, 2>;
 template <bool POT> using S1 = mixk::MixShape<128, 2, POT, true, false, 2, 2>;
-template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 2, 4>;
+template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 1, 4>;
 template <bool POT> using S3 = mixk::MixShape<256, 1, POT, true, false, 4, 2>;
-template <bool POT> using S4 = mixk::MixShape<64, 3, POT, false, true, 2, 5>;
-template <bool POT> using S5 = mixk::MixShape<32, 4, POT, false, true, 2, 8>;
+template <bool POT> using S4 = mixk::MixShape<64, 3, POT, false, true, 1, 5>;
+template <bool POT> using S5 = mixk::MixShape<32, 4, POT, false, true, 1, 8>;
 
 template <class Sh>
 cudaError_t launch_shape(const ForceArgs& a, int grid, cudaStream_t st) {

@@ -3,7 +3,7 @@
 //
 // Computes, for each target i, Eq. 1 with the softening of Eq. 2 plus the
 // jerk and potential:
-//   a_i  =  sum_j m_j d / s^3,   jerk_i = sum_j m_j (w / s^3 - 3 (d.w) d / s^5),
+//   a_i  =  sum_j m_j d / s^3,   jerk_i = sum_j m_j (w - 3 (d.w / s^2) d) / s^3,
 //   pot_i = -sum_j m_j / s,       d = r_j - r_i, w = v_j - v_i, s^2 = d.d + eps^2
 // (G applied on output).
 //
@@ -25,8 +25,11 @@
 //     the relative accuracy of the FP32 arithmetic after it, without the
 //     cancellation that absolute FP32 positions suffer.
 // Everything after the separation is FP32 (hardware rsqrt and reciprocal);
-// sums are accumulated per tile in FP32 and folded into a compensated
-// (hi, lo) FP32 pair per tile (two-sum), then combined in FP64.
+// the jerk term is formed per pair as m (w + t d) / s^3 with t = -3 d.w / s^2
+// (its rounding is relative to |w| + 3 |d.w| |d| / s^2, the magnitude of the
+// two terms taken apart); sums are accumulated per tile in FP32 and folded
+// into a compensated (hi, lo) FP32 pair per tile (two-sum), then combined in
+// FP64.
 //
 // GB300 mapping:
 //   * persistent CTAs loop over work items (cluster, i-tile, j-chunk); the
@@ -74,10 +77,13 @@ struct MixShape {
 // What the source loop needs of one target in registers; the target's
 // absolute double-single position and its slot stay in shared memory.
 struct Target {
-  f2 nvx, nvy, nvz;                                 // -v_i as broadcast pairs
-  f2 ex, ey, ez;                                    // hi part of c_J - r_i (broadcast)
-  f2 ax, ay, az, j1x, j1y, j1z, j2x, j2y, j2z, pt;  // per-tile sums (2 lanes)
+  f2 nvx, nvy, nvz;              // -v_i as broadcast pairs
+  f2 ex, ey, ez;                 // hi part of c_J - r_i (broadcast)
+  f2 ax, ay, az, jx, jy, jz, pt; // per-tile sums (2 lanes)
 };
+
+// compensated totals per target: a (3), jerk (3), potential
+constexpr int kTotComps = 7;
 
 // Per-thread shared-memory record of a target: r_i as double-single and its
 // source slot (-1: no target); component-major so a warp's loads are
@@ -134,17 +140,13 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
   const f2 mri = f2_mul(m, rinv);
   const f2 mr3 = f2_mul(mri, r2inv);
   if (Sh::POT) s.pt = f2_add(s.pt, mri);
-  const f2 u = f2_mul(rv, r2inv);
-  const f2 bb = f2_mul(u, mr3);
+  const f2 t = f2_mul(f2_mul(rv, r2inv), f2_pack(-3.f, -3.f));  // -3 d.w / s^2
   s.ax = f2_fma(mr3, dx, s.ax);
   s.ay = f2_fma(mr3, dy, s.ay);
   s.az = f2_fma(mr3, dz, s.az);
-  s.j1x = f2_fma(mr3, wx, s.j1x);
-  s.j1y = f2_fma(mr3, wy, s.j1y);
-  s.j1z = f2_fma(mr3, wz, s.j1z);
-  s.j2x = f2_fma(bb, dx, s.j2x);
-  s.j2y = f2_fma(bb, dy, s.j2y);
-  s.j2z = f2_fma(bb, dz, s.j2z);
+  s.jx = f2_fma(mr3, f2_fma(t, dx, wx), s.jx);
+  s.jy = f2_fma(mr3, f2_fma(t, dy, wy), s.jy);
+  s.jz = f2_fma(mr3, f2_fma(t, dz, wz), s.jz);
 }
 
 // Far cell: d = dh_j + eh.  NG > 0: a full cell with a compile-time trip
@@ -201,14 +203,14 @@ __device__ __forceinline__ float lanes_sum(f2& v) {
   return p.x + p.y;
 }
 
-// Compensated totals of one target: 10 (hi, lo) pairs, in registers or in
-// shared memory (one column per thread).
+// Compensated totals of one target: kTotComps (hi, lo) pairs, in registers
+// or in shared memory (one column per thread).
 template <bool SMT, int NT>
 struct Totals {
-  float h[10], l[10];
+  float h[kTotComps], l[kTotComps];
   __device__ __forceinline__ void zero(float*) {
 #pragma unroll
-    for (int c = 0; c < 10; ++c) h[c] = l[c] = 0.f;
+    for (int c = 0; c < kTotComps; ++c) h[c] = l[c] = 0.f;
   }
   __device__ __forceinline__ void add(float*, int c, float x) { two_sum_acc(h[c], l[c], x); }
   __device__ __forceinline__ double get(float*, int c) const { return (double)h[c] + (double)l[c]; }
@@ -218,7 +220,20 @@ struct Totals<true, NT> {
   // column of this thread: col[(2 c) NT] = hi, col[(2 c + 1) NT] = lo
   __device__ __forceinline__ void zero(float* col) {
 #pragma unroll
-    for (int c = 0; c < 20; ++c) col[c * NT] = 0.f;
+    for (int c = 0; c < 2 * kTotComps; ++c) col[c * NT] = 0.f;
+  }
+  // components c, c + 1 at once: packed two-sum of x = (x_c, x_c+1)
+  __device__ __forceinline__ void add2(float* col, int c, f2 x) {
+    const f2 h = f2_pack(col[(2 * c) * NT], col[(2 * c + 2) * NT]);
+    f2 l = f2_pack(col[(2 * c + 1) * NT], col[(2 * c + 3) * NT]);
+    const f2 sm = f2_add(h, x);
+    const f2 bp = f2_sub(sm, h);
+    l = f2_add(l, f2_add(f2_sub(h, f2_sub(sm, bp)), f2_sub(x, bp)));
+    const float2 hh = f2_unpack(sm), ll = f2_unpack(l);
+    col[(2 * c) * NT] = hh.x;
+    col[(2 * c + 2) * NT] = hh.y;
+    col[(2 * c + 1) * NT] = ll.x;
+    col[(2 * c + 3) * NT] = ll.y;
   }
   __device__ __forceinline__ void add(float* col, int c, float x) {
     float hi = col[(2 * c) * NT], lo = col[(2 * c + 1) * NT];
@@ -231,18 +246,29 @@ struct Totals<true, NT> {
   }
 };
 
+// (a.x + a.y, b.x + b.y), clearing a and b
+__device__ __forceinline__ f2 lanes_sum2(f2& a, f2& b) {
+  const float2 pa = f2_unpack(a), pb = f2_unpack(b);
+  a = 0ull;
+  b = 0ull;
+  return f2_add(f2_pack(pa.x, pb.x), f2_pack(pa.y, pb.y));
+}
+
 template <class Sh>
 __device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT>& T, float* col) {
-  T.add(col, 0, lanes_sum(s.ax));
-  T.add(col, 1, lanes_sum(s.ay));
-  T.add(col, 2, lanes_sum(s.az));
-  T.add(col, 3, lanes_sum(s.j1x));
-  T.add(col, 4, lanes_sum(s.j1y));
-  T.add(col, 5, lanes_sum(s.j1z));
-  T.add(col, 6, lanes_sum(s.j2x));
-  T.add(col, 7, lanes_sum(s.j2y));
-  T.add(col, 8, lanes_sum(s.j2z));
-  if (Sh::POT) T.add(col, 9, lanes_sum(s.pt));
+  if constexpr (Sh::SMT) {  // packed two-sums, two components at a time
+    T.add2(col, 0, lanes_sum2(s.ax, s.ay));
+    T.add2(col, 2, lanes_sum2(s.az, s.jx));
+    T.add2(col, 4, lanes_sum2(s.jy, s.jz));
+  } else {
+    T.add(col, 0, lanes_sum(s.ax));
+    T.add(col, 1, lanes_sum(s.ay));
+    T.add(col, 2, lanes_sum(s.az));
+    T.add(col, 3, lanes_sum(s.jx));
+    T.add(col, 4, lanes_sum(s.jy));
+    T.add(col, 5, lanes_sum(s.jz));
+  }
+  if (Sh::POT) T.add(col, 6, lanes_sum(s.pt));
 }
 
 // Tile t0 .. t0 + cnt of the source slots (cnt a multiple of 4) plus its
@@ -264,7 +290,7 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
   __shared__ __align__(16) float4 rec[2][kTileRecF4];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int abort_flag;
-  __shared__ float tot_sh[Sh::SMT ? IPT * 20 * NT : 1];
+  __shared__ float tot_sh[Sh::SMT ? IPT * 2 * kTotComps * NT : 1];
   __shared__ TargetPosSh<IPT, NT> tpos;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -344,10 +370,9 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       tpos.slot[r][tid] = slot_r;
       tg[r].nvx = bcast(-vx); tg[r].nvy = bcast(-vy); tg[r].nvz = bcast(-vz);
       tg[r].ax = tg[r].ay = tg[r].az = 0ull;
-      tg[r].j1x = tg[r].j1y = tg[r].j1z = 0ull;
-      tg[r].j2x = tg[r].j2y = tg[r].j2z = 0ull;
+      tg[r].jx = tg[r].jy = tg[r].jz = 0ull;
       tg[r].pt = 0ull;
-      tot[r].zero(tot_sh + r * 20 * NT + tid);
+      tot[r].zero(tot_sh + r * 2 * kTotComps * NT + tid);
     }
 
     const int64_t ntile = ceil_div64(j1 - j0, JT);
@@ -414,18 +439,15 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
             ds_sub(ch.x, cl.x, tp.xh, tp.xl, h, lx);
             ds_sub(ch.y, cl.y, tp.yh, tp.yl, h, ly);
             ds_sub(ch.z, cl.z, tp.zh, tp.zl, h, lz);
-            if (tp.slot >= c0 && tp.slot < c0 + 4 * ngq)  // the target's own cell
-              tile_near_one<Sh, true>(cell, ngq, c0, tg[r], bcast(lx), bcast(ly), bcast(lz),
-                                      tp.slot, eps2);
-            else
-              tile_near_one<Sh, false>(cell, ngq, c0, tg[r], bcast(lx), bcast(ly), bcast(lz),
-                                       -1, eps2);
+            // the slot test excludes j == i where the target's own cell is near
+            tile_near_one<Sh, true>(cell, ngq, c0, tg[r], bcast(lx), bcast(ly), bcast(lz),
+                                    tp.slot, eps2);
           }
         }
       }
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < IPT; ++r) flush<Sh>(tg[r], tot[r], tot_sh + r * 20 * NT + tid);
+        for (int r = 0; r < IPT; ++r) flush<Sh>(tg[r], tot[r], tot_sh + r * 2 * kTotComps * NT + tid);
       }
       __syncthreads();
       if (abort_flag) goto drain;
@@ -443,15 +465,15 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
 #pragma unroll
     for (int r = 0; r < IPT; ++r) {
       if (!valid[r]) continue;
-      float* col = tot_sh + r * 20 * NT + tid;
+      float* col = tot_sh + r * 2 * kTotComps * NT + tid;
       double v[kPartialComps];
       v[0] = tot[r].get(col, 0);
       v[1] = tot[r].get(col, 1);
       v[2] = tot[r].get(col, 2);
-      v[3] = tot[r].get(col, 3) - 3.0 * tot[r].get(col, 6);
-      v[4] = tot[r].get(col, 4) - 3.0 * tot[r].get(col, 7);
-      v[5] = tot[r].get(col, 5) - 3.0 * tot[r].get(col, 8);
-      v[6] = Sh::POT ? -tot[r].get(col, 9) : 0.0;
+      v[3] = tot[r].get(col, 3);
+      v[4] = tot[r].get(col, 4);
+      v[5] = tot[r].get(col, 5);
+      v[6] = Sh::POT ? -tot[r].get(col, 6) : 0.0;
       const int32_t ql = wp * 32 * IPT + r * 32 + ln;
       if (B == 1) {
         int64_t srow = a0 + it * NI + ql;
