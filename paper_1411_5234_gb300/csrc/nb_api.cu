@@ -22,7 +22,7 @@ constexpr int kEnergyBlocks = 304;
 
 struct Layout {
   size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
-      src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, bfac, esum,
+      src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, wt_off, wide_cnt, bfac, esum,
       status, counters, t_end, tiles, toff, sperm, sinv, mark, rows, total;
   int64_t S, part_items, n_tiles;
 };
@@ -62,6 +62,8 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
   L.t_min = take(c, 8 * (size_t)K);
   L.act_off = take(c, 4 * ((size_t)K + 1));
   L.item_off = take(c, 4 * ((size_t)K + 1));
+  L.wt_off = take(c, 4 * ((size_t)K + 1));
+  L.wide_cnt = take(c, 4 * (size_t)wide_counter_entries(L.part_items));
   L.bfac = take(c, 4 * (size_t)K);
   L.esum = take(c, 8 * (2 * (size_t)kEnergyBlocks + 2));
   L.status = take(c, 4);
@@ -181,7 +183,7 @@ struct nb_ctx {
   Dev d;
   Layout L{};
   cudaStream_t st = nullptr;
-  int grid_mix = 0, grid_f64 = 0;
+  int grid_mix = 0, grid_f64 = 0, sms = 0;
   std::vector<int64_t> off_host;
   std::vector<double> mass_host;
   std::vector<int32_t> sperm_host;  // source slot order (for the autotuner's target lists)
@@ -214,6 +216,8 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, doub
   a.active = active;
   a.act_off = c->d.act_off;
   a.item_off = c->d.item_off;
+  a.wt_off = c->d.wt_off;
+  a.wide_cnt = c->d.wide_cnt;
   a.bfac = c->d.bfac;
   a.sinv = c->d.sinv;
   a.tiles = c->d.tiles;
@@ -322,7 +326,7 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
     c->ev_pending.push_back(ev);
   }
   return launch_reduce(fa, f64 ? kF64NI : force_mixed_ni(c->cfg.variant), !pot_only, m_bound,
-                       c->st);
+                       c->sms, c->st);
 }
 
 cudaError_t enqueue_block_step(nb_ctx* c) {
@@ -461,6 +465,8 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   d.t_min = reinterpret_cast<int64_t*>(w + c->L.t_min);
   d.act_off = reinterpret_cast<int32_t*>(w + c->L.act_off);
   d.item_off = reinterpret_cast<int32_t*>(w + c->L.item_off);
+  d.wt_off = reinterpret_cast<int32_t*>(w + c->L.wt_off);
+  d.wide_cnt = reinterpret_cast<int32_t*>(w + c->L.wide_cnt);
   d.bfac = reinterpret_cast<int32_t*>(w + c->L.bfac);
   d.esum = reinterpret_cast<double*>(w + c->L.esum);
   d.status = reinterpret_cast<uint32_t*>(w + c->L.status);
@@ -482,6 +488,11 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   }
   c->grid_mix = sms * force_mixed_ctas_per_sm(cfg->variant);
   c->grid_f64 = sms * force_fp64_ctas_per_sm();
+  c->sms = sms;
+  if (integrator_setup() != cudaSuccess) {
+    delete c;
+    return NB_ECUDA;
+  }
 
   // host staging of the initial state
   std::vector<double> p4(4 * N), v4(4 * N, 0.0);
@@ -521,6 +532,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
         cudaMemsetAsync(d.t, 0, 8 * N, st) || cudaMemsetAsync(d.level, 0, 4 * N, st) ||
         cudaMemsetAsync(d.t_cur, 0, 8 * n_clusters, st) ||
         cudaMemsetAsync(d.status, 0, 4, st) || cudaMemsetAsync(d.counters, 0, 32, st) ||
+        cudaMemsetAsync(d.wide_cnt, 0, 4 * (size_t)wide_counter_entries(c->L.part_items), st) ||
         cudaMemsetAsync(d.mark, 0xff, 4 * N, st)) {
       rc = NB_ECUDA;
       break;

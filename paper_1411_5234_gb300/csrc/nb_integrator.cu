@@ -144,7 +144,7 @@ __global__ void k_scan(Dev d, int32_t nblk) {
 __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* t_tgt,
                                                           int64_t t_fixed, int T, int write_mix,
                                                           int write64, int count_due) {
-  __shared__ double shd[kMixJT / 32];
+  __shared__ float shd[kMixJT / 32];
   __shared__ int32_t shi[32];
   const int32_t tile = blockIdx.x;
   const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
@@ -226,18 +226,20 @@ __global__ void k_plan(Dev d, PlanArgs p) {
         bg = p.forced_b;
       } else {
         // fill the persistent grid, then pick the split whose last round of
-        // work items is fullest
-        // a few candidates above the fill point, 32-bit arithmetic (the
-        // per-cluster clamp below bounds B by the cluster's tile count anyway)
+        // work items is fullest: a few candidates above the fill point (the
+        // per-cluster clamp below bounds B by the cluster's tile count), in
+        // 32-bit integers and FP32, since one thread's FP64 division costs
+        // microseconds on this part.  n b = (q g + r) b items take
+        // q b + ceil(r b / g) rounds, and r b < 10 g fits 32 bits.
         const uint32_t g = static_cast<uint32_t>(p.grid);
         const uint32_t n = nit > (1ull << 30) ? (1u << 30) : static_cast<uint32_t>(nit);
         const uint32_t b0 = n >= g ? 1u : (g + n - 1) / n;
-        double best = -1.0;
+        const uint32_t q = n / g, r = n - q * g;
+        float best = -1.f;
         for (uint32_t b = b0; b <= b0 + 8; ++b) {
-          const uint64_t items = (uint64_t)n * b;
-          const uint64_t rounds = (items + g - 1) / g;
-          const double eff = (double)items / (double)(rounds * g);
-          if (eff > best + 1e-3) { best = eff; bg = b; }
+          const uint32_t rounds = q * b + (r * b + g - 1) / g;
+          const float e = __fdiv_rn((float)n * (float)b, (float)rounds * (float)g);
+          if (e > best + 1e-3f) { best = e; bg = b; }
         }
       }
       const int64_t cap = max((int64_t)1, p.part_items / (int64_t)nit);
@@ -251,10 +253,10 @@ __global__ void k_plan(Dev d, PlanArgs p) {
   }
   __syncthreads();
   const int32_t bg = bg_sh;
-  int32_t carry = 0;
+  int32_t carry = 0, wcarry = 0;
   for (int32_t k0 = 0; k0 < K; k0 += blockDim.x) {
     const int32_t k = k0 + threadIdx.x;
-    int32_t items = 0;
+    int32_t items = 0, wide = 0;
     if (k < K) {
       const int64_t mk = d.act_off[k + 1] - d.act_off[k];
       const int64_t Sk = d.soff[k + 1] - d.soff[k];
@@ -263,27 +265,44 @@ __global__ void k_plan(Dev d, PlanArgs p) {
       B = ceil_div64(Sk, chunk_len(Sk, B, p.JT));  // every chunk non-empty
       d.bfac[k] = static_cast<int32_t>(B);
       items = static_cast<int32_t>(ceil_div64(mk, p.NI) * B);
+      if (B > kReduceSerial)  // (i-tile, row segment) units of k_reduce_wide
+        wide = static_cast<int32_t>(ceil_div64(mk, p.NI) * ceil_div64(B, kWideRows));
       if (p.step_mode) {
         const int64_t tn = d.t_min[k];
         if (tn != LLONG_MAX) d.t_cur[k] = tn;
         d.t_min[k] = LLONG_MAX;
       }
     }
-    int32_t tot;
+    int32_t tot, wtot;
     const int32_t ex = block_excl_scan(items, shi, &tot);
-    if (k < K) d.item_off[k] = carry + ex;
+    const int32_t wex = block_excl_scan(wide, shi, &wtot);
+    if (k < K) {
+      d.item_off[k] = carry + ex;
+      d.wt_off[k] = wcarry + wex;
+    }
     carry += tot;
+    wcarry += wtot;
   }
-  if (threadIdx.x == 0) d.item_off[K] = carry;
+  if (threadIdx.x == 0) {
+    d.item_off[K] = carry;
+    d.wt_off[K] = wcarry;
+  }
 }
 
 // Fixed-order sum of the B_k partials of every target whose cluster was
-// split.  Each lane owns one target of its warp's 32 consecutive targets:
-// with B_k <= kReduceSerial the lane sums b = 0 .. B_k - 1 in order; larger
-// B_k are taken one target at a time by the whole warp (lane l sums
-// b = l, l + 32, ... in order, then a fixed butterfly).  Deterministic.
-constexpr int kReduceSerial = 16;
-
+// split (Sec. 2 item 3); the order depends on B_k alone.
+//   k_reduce (1 < B_k <= kReduceSerial): each lane owns one target and sums
+//     b = 0 .. B_k - 1 in order (the lanes of a warp read consecutive targets
+//     of one partial row).
+//   k_reduce_wide (B_k > kReduceSerial: few active targets split over many
+//     source chunks): the partial rows of an i-tile are cut into segments of
+//     kWideRows rows; one CTA of kWideRows warps takes one segment of one
+//     block of 32 targets, warp r holding row r, and combines the rows in
+//     pairs (r, r + o) for o = 16, 8, 4, 2, 1.  With one segment that is the
+//     result; otherwise the CTA writes its segment sum over the segment's
+//     first row, and the last CTA of the block (arrival counter) adds the
+//     segment sums in segment order.  GB300 runs FP64 at ~2 lanes per SM per
+//     clock, so the segments spread the additions over many SMs.
 __device__ __forceinline__ void write_reduced(const ForceArgs& a, int32_t s, const double* v,
                                               int with_acc) {
   const int64_t row = a.rows ? (int64_t)a.rows[s] : (int64_t)s;
@@ -296,51 +315,123 @@ __device__ __forceinline__ void write_reduced(const ForceArgs& a, int32_t s, con
 
 __global__ void k_reduce(ForceArgs a, int NI, int with_acc) {
   const int32_t m = a.act_off[a.K];
-  const int lane = threadIdx.x & 31;
-  const int32_t nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int32_t s0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; s0 < m;
-       s0 += nwarps * 32) {
-    const int32_t s = s0 + lane;
-    int32_t B = 0, w0 = 0, q = 0;
-    if (s < m) {
-      const int32_t k = upper_bound_i32(a.act_off, a.K + 1, s) - 1;
-      B = a.bfac[k];
-      const int32_t local = s - a.act_off[k];
-      const int32_t it = local / NI;
-      q = local - it * NI;
-      w0 = a.item_off[k] + it * B;
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {
+    const int32_t k = upper_bound_i32(a.act_off, a.K + 1, s) - 1;
+    const int32_t B = a.bfac[k];
+    if (B <= 1 || B > kReduceSerial) continue;
+    const int32_t local = s - a.act_off[k];
+    const int32_t it = local / NI;
+    const int32_t q = local - it * NI;
+    const int32_t w0 = a.item_off[k] + it * B;
+    double v[kPartialComps];
+#pragma unroll
+    for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
+    for (int32_t b = 0; b < B; ++b) {
+      const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
+#pragma unroll
+      for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
     }
-    if (B > 1 && B <= kReduceSerial) {
-      double v[kPartialComps];
+    write_reduced(a, s, v, with_acc);
+  }
+}
+
+constexpr size_t kWideSmem = sizeof(double) * kPartialComps * kWideRows * 32;
+
+__global__ void __launch_bounds__(32 * kWideRows) k_reduce_wide(ForceArgs a, int NI,
+                                                                int with_acc) {
+  extern __shared__ double red[];  // [component][row r][lane]
+  __shared__ int last_sh;
+  const int32_t K = a.K;
+  const int32_t cbs = NI / 32;
+  const int32_t units = a.wt_off[K] * cbs;
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  for (int32_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int32_t ws = u / cbs;             // (i-tile, segment) unit
+    const int32_t cb = u - ws * cbs;        // block of 32 targets
+    const int32_t k = upper_bound_i32(a.wt_off, K + 1, ws) - 1;
+    const int32_t B = a.bfac[k];
+    const int32_t nseg = (B + kWideRows - 1) / kWideRows;
+    const int32_t lw = ws - a.wt_off[k];
+    const int32_t it = lw / nseg;
+    const int32_t g = lw - it * nseg;
+    const int32_t m_k = a.act_off[k + 1] - a.act_off[k];
+    const int32_t q = cb * 32 + lane;
+    const int32_t local = it * NI + q;
+    const bool valid = local < m_k;
+    const int32_t w0 = a.item_off[k] + it * B;
+    const int32_t b = g * kWideRows + r;
+    double v[kPartialComps];
 #pragma unroll
-      for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
-      for (int32_t b = 0; b < B; ++b) {
-        const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
+    for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
+    if (valid && b < B) {
+      const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
 #pragma unroll
-        for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
+      for (int c = 0; c < kPartialComps; ++c) v[c] = P[(size_t)c * NI];
+    }
+#pragma unroll
+    for (int c = 0; c < kPartialComps; ++c) red[(c * kWideRows + r) * 32 + lane] = v[c];
+    __syncthreads();
+    for (int o = kWideRows / 2; o > 0; o >>= 1) {
+      if (r < o) {
+#pragma unroll
+        for (int c = 0; c < kPartialComps; ++c)
+          red[(c * kWideRows + r) * 32 + lane] += red[(c * kWideRows + r + o) * 32 + lane];
       }
-      write_reduced(a, s, v, with_acc);
+      __syncthreads();
     }
-    unsigned big = __ballot_sync(0xffffffffu, B > kReduceSerial);
-    while (big) {
-      const int src = __ffs(big) - 1;
-      big &= big - 1;
-      const int32_t Bs = __shfl_sync(0xffffffffu, B, src);
-      const int32_t w0s = __shfl_sync(0xffffffffu, w0, src);
-      const int32_t qs = __shfl_sync(0xffffffffu, q, src);
-      double v[kPartialComps];
+    if (nseg == 1) {
+      if (r == 0 && valid) {
 #pragma unroll
-      for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
-      for (int32_t b = lane; b < Bs; b += 32) {
-        const double* P = a.partials + (size_t)(w0s + b) * kPartialComps * NI + qs;
-#pragma unroll
-        for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
+        for (int c = 0; c < kPartialComps; ++c) v[c] = red[(c * kWideRows) * 32 + lane];
+        write_reduced(a, a.act_off[k] + local, v, with_acc);
       }
+    } else {
+      // segment sum over the segment's first row (only this CTA reads or
+      // writes those columns of that row until the block's last CTA)
+      if (r == 0) {
+        if (valid) {
+          double* P0 = a.partials + (size_t)(w0 + g * kWideRows) * kPartialComps * NI + q;
 #pragma unroll
-      for (int c = 0; c < kPartialComps; ++c)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-      if (lane == 0) write_reduced(a, s0 + src, v, with_acc);
+          for (int c = 0; c < kPartialComps; ++c) P0[(size_t)c * NI] = red[(c * kWideRows) * 32 + lane];
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      int32_t* cnt = a.wide_cnt + (size_t)(a.wt_off[k] + it * nseg) * cbs + cb;
+      if (threadIdx.x == 0) last_sh = atomicAdd(cnt, 1) == nseg - 1;
+      __syncthreads();
+      if (last_sh) {
+        // warp r < kPartialComps adds component r of the segment sums in
+        // segment order, eight loads in flight at a time
+        if (r < kPartialComps) {
+          __threadfence();
+          double acc = 0.0;
+          for (int32_t h0 = 0; h0 < nseg; h0 += 8) {
+            double x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const double* P0 =
+                  a.partials + (size_t)(w0 + (h0 + j) * kWideRows) * kPartialComps * NI + q;
+              x[j] = (valid && h0 + j < nseg) ? __ldcg(P0 + (size_t)r * NI) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (h0 + j < nseg) acc += x[j];
+          }
+          red[r * 32 + lane] = acc;
+        }
+        __syncthreads();
+        if (r == 0) {
+          if (valid) {
+#pragma unroll
+            for (int c = 0; c < kPartialComps; ++c) v[c] = red[c * 32 + lane];
+            write_reduced(a, a.act_off[k] + local, v, with_acc);
+          }
+          if (lane == 0) *cnt = 0;  // ready for the next launch
+        }
+      }
     }
+    __syncthreads();  // red[] and last_sh are rewritten by the next unit
   }
 }
 
@@ -408,7 +499,12 @@ __global__ void k_correct(Dev d, CorrectArgs c) {
     // the Hermite fit's divisions as multiplications by 1/t^2, 1/t^3 and
     // the Taylor coefficients (FP64 division is a long sequence here)
     const double t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
-    const double it2 = 1.0 / t2, it3 = it2 / t;
+    // a block step's t is a power of two: its reciprocals are exact scalings
+    // (the same values the divisions give), without FP64 divisions
+    int te;
+    const bool pow2 = frexp(t, &te) == 0.5;
+    const double it2 = pow2 ? ldexp(1.0, 2 - 2 * te) : 1.0 / t2;
+    const double it3 = pow2 ? ldexp(1.0, 3 - 3 * te) : it2 / t;
     const double c24 = t4 * (1.0 / 24.0), c120 = t5 * (1.0 / 120.0), c6 = t3 * (1.0 / 6.0);
     double x1[3], v1[3], a2e[3], a3[3];
 #pragma unroll
@@ -601,13 +697,22 @@ cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
-                          cudaStream_t st) {
-  // one lane per target, warps of 32 consecutive targets
+                          int wide_grid, cudaStream_t st) {
+  // one lane per target for small splits; the wide kernel for large ones
+  // (both exit at once when the plan gave them nothing to do)
   k_reduce<<<blocks_for(m_bound, 256), 256, 0, st>>>(a, NI, with_acc ? 1 : 0);
+  k_reduce_wide<<<wide_grid > 0 ? wide_grid : 1, 32 * kWideRows, kWideSmem, st>>>(
+      a, NI, with_acc ? 1 : 0);
   return cudaGetLastError();
 }
+cudaError_t integrator_setup() {
+  return cudaFuncSetAttribute(k_reduce_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kWideSmem));
+}
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {
-  k_correct<<<blocks_for(m_bound, 128), 128, 0, st>>>(d, c);
+  // 32-thread CTAs: a few hundred active particles still spread over many
+  // SMs (the corrector is FP64 arithmetic, ~2 lanes per SM per clock)
+  k_correct<<<blocks_for(m_bound, 32), 32, 0, st>>>(d, c);
   return cudaGetLastError();
 }
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,

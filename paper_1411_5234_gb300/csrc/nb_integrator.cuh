@@ -6,58 +6,78 @@
 
 namespace nb {
 
+// i-split factors up to kReduceSerial are reduced by one lane per target
+// (k_reduce); larger ones by k_reduce_wide in segments of kWideRows partial
+// rows (one per warp of its CTA).
+constexpr int kReduceSerial = 16;
+constexpr int kWideRows = 32;
+
+// Entries of the k_reduce_wide arrival counters for a partial-sum buffer of
+// part_items work items.  The plan keeps sum_k T_k B_k <= part_items (T_k
+// i-tiles of cluster k), so the units (i-tile, row segment) of clusters with
+// B_k > kReduceSerial, sum_k T_k ceil(B_k / kWideRows), stay below
+// part_items / kWideRows + part_items / (kReduceSerial + 1); one counter per
+// unit and block of 32 targets (at most kMixNI / 32 blocks).
+constexpr int64_t wide_counter_entries(int64_t part_items) {
+  return (part_items / kWideRows + part_items / (kReduceSerial + 1) + 2) * (kMixNI / 32);
+}
+
 // Min or max of v over the threads of one cell (kMixJD = 64 threads, two
 // warps) of a CTA of kMixJT threads; every thread gets its cell's result.
-// `sh` holds >= kMixJT / 32 doubles.
-__device__ __forceinline__ double nb_half_reduce_d(double v, bool is_max, double* sh) {
+// `sh` holds >= kMixJT / 32 floats.
+__device__ __forceinline__ float nb_half_reduce_f(float v, bool is_max, float* sh) {
   static_assert(kMixJD == 64 && kMixJT % kMixJD == 0, "two warps per cell");
   for (int o = 16; o > 0; o >>= 1) {
-    const double u = __shfl_xor_sync(0xffffffffu, v, o);
-    v = is_max ? fmax(v, u) : fmin(v, u);
+    const float u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmaxf(v, u) : fminf(v, u);
   }
   const int wid = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) sh[wid] = v;
   __syncthreads();
-  const double a = sh[wid & ~1], b = sh[wid | 1];
+  const float a = sh[wid & ~1], b = sh[wid | 1];
   __syncthreads();
-  return is_max ? fmax(a, b) : fmin(a, b);
+  return is_max ? fmaxf(a, b) : fminf(a, b);
 }
 
 // Write one mixed source tile (one CTA of kMixJT threads, one slot each).
 // The tile holds kMixCells cells of kMixJD slots; for each cell: centre c = the
-// midpoint of its valid particles' bounding box, rounded to a double-single
-// pair (ch, cl), radius h = max |r_j - c| (rounded up).  Each valid slot
-// stores its double-single offset r_j - c from its cell's centre, its mass
-// and FP32 velocity; pad slots (in == true, valid == false) hold massless
-// dummies far away.  Record of tile t: float4 [kTileRecF4 t + 2q] = (ch, h)
-// and [kTileRecF4 t + 2q + 1] = (cl, 0) for cell q.  Every thread must call
-// this.
+// midpoint of its valid particles' bounding box, taken in FP32 (c is only a
+// reference point, exactly representable as a float), radius h >= max |r_j - c|.
+// Each valid slot stores its double-single offset r_j - c (formed in FP64) from
+// its cell's centre, its mass and FP32 velocity; pad slots (in == true,
+// valid == false) hold massless dummies far away.  Record of tile t: float4
+// [kTileRecF4 t + 2q] = (c, h) and [kTileRecF4 t + 2q + 1] = (0, 0, 0, 0)
+// (the low part of a double-single centre) for cell q.  The FP64 work per slot
+// is the offset and its split; the box and the radius use the FP32 pipe.
+// Every thread must call this.
 __device__ __forceinline__ void build_mixed_tile(float4* src, float4* tiles, int64_t tile,
                                                  int64_t s, bool in, bool valid, double3 x,
-                                                 double m, double3 v, double* sh) {
-  const double inf = CUDART_INF;
-  const double lx = nb_half_reduce_d(valid ? x.x : inf, false, sh);
-  const double ly = nb_half_reduce_d(valid ? x.y : inf, false, sh);
-  const double lz = nb_half_reduce_d(valid ? x.z : inf, false, sh);
-  const double hx = nb_half_reduce_d(valid ? x.x : -inf, true, sh);
-  const double hy = nb_half_reduce_d(valid ? x.y : -inf, true, sh);
-  const double hz = nb_half_reduce_d(valid ? x.z : -inf, true, sh);
+                                                 double m, double3 v, float* sh) {
+  const float inf = CUDART_INF_F;
+  const float fx = __double2float_rn(x.x), fy = __double2float_rn(x.y),
+              fz = __double2float_rn(x.z);
+  const float lx = nb_half_reduce_f(valid ? fx : inf, false, sh);
+  const float ly = nb_half_reduce_f(valid ? fy : inf, false, sh);
+  const float lz = nb_half_reduce_f(valid ? fz : inf, false, sh);
+  const float hx = nb_half_reduce_f(valid ? fx : -inf, true, sh);
+  const float hy = nb_half_reduce_f(valid ? fy : -inf, true, sh);
+  const float hz = nb_half_reduce_f(valid ? fz : -inf, true, sh);
   const bool any = lx <= hx;
-  const double cx = any ? 0.5 * (lx + hx) : 0.0, cy = any ? 0.5 * (ly + hy) : 0.0,
-               cz = any ? 0.5 * (lz + hz) : 0.0;
-  const float chx = __double2float_rn(cx), chy = __double2float_rn(cy), chz = __double2float_rn(cz);
-  const float clx = __double2float_rn(cx - (double)chx), cly = __double2float_rn(cy - (double)chy),
-              clz = __double2float_rn(cz - (double)chz);
-  const double ux = (double)chx + (double)clx, uy = (double)chy + (double)cly,
-               uz = (double)chz + (double)clz;  // the centre as represented
-  const double dx = x.x - ux, dy = x.y - uy, dz = x.z - uz;
-  const double r = valid ? sqrt(dx * dx + dy * dy + dz * dz) : 0.0;
-  const double h = nb_half_reduce_d(r, true, sh);
+  // lx + hx cannot overflow for positions far below FLT_MAX
+  const float chx = any ? 0.5f * (lx + hx) : 0.f, chy = any ? 0.5f * (ly + hy) : 0.f,
+              chz = any ? 0.5f * (lz + hz) : 0.f;
+  const double dx = x.x - (double)chx, dy = x.y - (double)chy, dz = x.z - (double)chz;
+  const float dxh = __double2float_rn(dx), dyh = __double2float_rn(dy),
+              dzh = __double2float_rn(dz);
+  // |r_j - c| from the rounded offsets, then rounded up by 2^-18 relative: a
+  // bound on the true distance (the FP32 rounding of the offsets and of the
+  // sum and square root stays below 2^-21 relative)
+  const float r = valid ? __fmul_ru(sqrtf(dxh * dxh + dyh * dyh + dzh * dzh), 1.0f + 0x1p-18f)
+                        : 0.f;
+  const float h = nb_half_reduce_f(r, true, sh);
   if (in) {
     float* g = reinterpret_cast<float*>(src + (s >> 2) * 10) + (s & 3);
     if (valid) {
-      const float dxh = __double2float_rn(dx), dyh = __double2float_rn(dy),
-                  dzh = __double2float_rn(dz);
       g[0] = dxh;
       g[4] = dyh;
       g[8] = dzh;
@@ -77,8 +97,8 @@ __device__ __forceinline__ void build_mixed_tile(float4* src, float4* tiles, int
   }
   if ((threadIdx.x & (kMixJD - 1)) == 0) {
     const int q = threadIdx.x / kMixJD;
-    tiles[kTileRecF4 * tile + 2 * q] = make_float4(chx, chy, chz, __double2float_ru(h));
-    tiles[kTileRecF4 * tile + 2 * q + 1] = make_float4(clx, cly, clz, 0.f);
+    tiles[kTileRecF4 * tile + 2 * q] = make_float4(chx, chy, chz, h);
+    tiles[kTileRecF4 * tile + 2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -111,8 +131,11 @@ cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, 
                            bool f64, bool count_due, cudaStream_t st);
 cudaError_t launch_compact(const Dev& d, int T, cudaStream_t st);
 cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st);
+// wide_grid: CTAs of the wide-split reduction (one per SM is enough)
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
-                          cudaStream_t st);
+                          int wide_grid, cudaStream_t st);
+// one-time kernel attributes (the wide reduction's dynamic shared memory)
+cudaError_t integrator_setup();
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st);
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,
                                cudaStream_t st);

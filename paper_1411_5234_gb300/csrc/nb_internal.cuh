@@ -73,6 +73,8 @@ struct Dev {
   int64_t *off = nullptr, *soff = nullptr;   // K + 1
   int64_t *t_cur = nullptr, *t_min = nullptr; // K
   int32_t *act_off = nullptr, *item_off = nullptr; // K + 1
+  int32_t* wt_off = nullptr;     // K + 1: (i-tile, row segment) units of k_reduce_wide
+  int32_t* wide_cnt = nullptr;   // k_reduce_wide arrival counters (zero between launches)
   int32_t* bfac = nullptr;       // K
   double* esum = nullptr;        // energy partial sums
   uint32_t* status = nullptr;
@@ -88,6 +90,8 @@ struct ForceArgs {
   const int32_t* active;    // target particle indices (nullptr: identity)
   const int32_t* act_off;   // target offsets per cluster (K + 1)
   const int32_t* item_off;  // work-item offsets per cluster (K + 1)
+  const int32_t* wt_off;    // offsets of the wide-split reduction units per cluster (K + 1)
+  int32_t* wide_cnt;        // arrival counters of the wide-split reduction
   const int32_t* bfac;      // i-split factor per cluster (K)
   const int32_t* sinv;      // source slot of each particle (nullptr: slot order = particle order)
   const float4* tiles;      // mixed source tile records

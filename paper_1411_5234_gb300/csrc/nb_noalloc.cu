@@ -51,6 +51,9 @@ constexpr size_t kSmallBytes = 4096;  // offsets, plan words, status, counters
 constexpr size_t kNoAllocBytes = kOffSmall + kSmallBytes;  // 6,705,664 bytes
 static_assert(kNoAllocBytes == 6705664, "documented size of the fixed array");
 
+static_assert(64 + wide_counter_entries(kNoAllocItems) <= (kSmallBytes - 256) / 4,
+              "the reduction counters fit in the small area");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Per-device set-up results.
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kMixJT) k_noalloc_pack_mix(const double* pos, 
                                                              const double* mass, int64_t n,
                                                              int64_t n_pad, float4* src,
                                                              float4* tiles) {
-  __shared__ double sh[kMixJT / 32];
+  __shared__ float sh[kMixJT / 32];
   const int64_t s = (int64_t)blockIdx.x * kMixJT + threadIdx.x;
   const bool in = s < n_pad, valid = s < n;
   double3 x = make_double3(0.0, 0.0, 0.0), v = make_double3(0.0, 0.0, 0.0);
@@ -128,6 +131,7 @@ int setup_device(DeviceSetup** out) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return NB_ECUDA;
+    if (integrator_setup() != cudaSuccess) return NB_ECUDA;
     s.base = static_cast<unsigned char*>(p);
     s.sms = sms;
     s.ready = true;
@@ -181,6 +185,8 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   d.part_items = kNoAllocItems;
   d.tiles = reinterpret_cast<float4*>(base + kOffTiles);
   d.toff = small32 + 16;     // 2 entries
+  d.wt_off = small32 + 20;   // 2 entries
+  d.wide_cnt = small32 + 64; // wide_counter_entries(kNoAllocItems), zero from load time
   const int32_t n_tiles = static_cast<int32_t>((n_pad + kMixJT - 1) / kMixJT);
 
   k_noalloc_setup<<<1, 32, 0, st>>>(n, n_pad, m, n_tiles, d.off, d.soff, d.act_off, d.toff,
@@ -210,6 +216,8 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   a.active = target_idx;
   a.act_off = d.act_off;
   a.item_off = d.item_off;
+  a.wt_off = d.wt_off;
+  a.wide_cnt = d.wide_cnt;
   a.bfac = d.bfac;
   a.sinv = nullptr;  // sources in particle order
   a.tiles = d.tiles;
@@ -232,7 +240,7 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   cudaError_t e = f64 ? launch_force_fp64(a, grid, kF64Full, st)
                       : launch_force_mixed(a, grid, pot != nullptr, 2, st);
   if (e != cudaSuccess) return NB_ECUDA;
-  if (launch_reduce(a, p.NI, true, m, st) != cudaSuccess) return NB_ECUDA;
+  if (launch_reduce(a, p.NI, true, m, ds->sms, st) != cudaSuccess) return NB_ECUDA;
   return NB_OK;
 }
 

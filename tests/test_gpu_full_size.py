@@ -72,7 +72,9 @@ def test_full_size_block_step_sampled(nb, cluster):
         sim.set_state(cl.pos, cl.vel, a0, j0, np.zeros(N, dtype=np.int64),
                       np.full(N, LEVEL, dtype=np.int32))
         sim.step(1)
-        pos1, vel1, acc1, jerk1, t1, lev1 = sim.get_state()
+        s = sim.get_state()
+        pos1, vel1, acc1, jerk1, t1, lev1 = (s[k] for k in ("pos", "vel", "acc", "jerk", "t",
+                                                            "level"))
         assert sim.status() == nb.NB_OK
         variant = sim.cfg.variant
     finally:
