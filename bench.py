@@ -468,7 +468,7 @@ def main():
     assert sim.status() == nbody.NB_OK, nbody.strerror(sim.status())
     inter_step = n * n
     value = job_rate(args.steps * inter_step, world, total_ms * 1e-3)
-    launches_per_step = 8   # tmin, predict, scan, scatter, plan, force, reduce, correct
+    launches_per_step = 7   # tmin, predict, scan+plan, scatter, force, reduce, correct
 
     clocks = clk.summary()
     force_avg_s = force_ms * 1e-3 / max(force_launches, 1)

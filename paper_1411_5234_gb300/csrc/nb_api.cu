@@ -304,9 +304,13 @@ cudaError_t prof_events(nb_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
 // act_off (and `active`, or the identity when null).
 cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows, double* acc,
                           int sa, double* jerk, int sj, double* pot, int sp, bool f64,
-                          int step_mode, int count, bool pot_only, int64_t m_bound) {
-  cudaError_t e = launch_plan(c->d, plan_args(c, f64, step_mode, count), c->st);
-  if (e != cudaSuccess) return e;
+                          int step_mode, int count, bool pot_only, int64_t m_bound,
+                          bool planned = false) {
+  cudaError_t e = cudaSuccess;
+  if (!planned) {
+    e = launch_plan(c->d, plan_args(c, f64, step_mode, count), c->st);
+    if (e != cudaSuccess) return e;
+  }
   ForceArgs fa = force_args(c, active, rows, acc, sa, jerk, sj, pot, sp, f64);
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->prof) {
@@ -336,13 +340,13 @@ cudaError_t enqueue_block_step(nb_ctx* c) {
   if (e != cudaSuccess) return e;
   e = launch_predict(c->d, c->d.t_min, 0, T, !f64, f64, true, c->st);
   if (e != cudaSuccess) return e;
-  e = launch_compact(c->d, T, c->st);
+  e = launch_scan_plan_scatter(c->d, plan_args(c, f64, 1, 1), T, c->st);
   if (e != cudaSuccess) return e;
   double* an = reinterpret_cast<double*>(c->d.acc_new);
   double* jn = reinterpret_cast<double*>(c->d.jerk_new);
   // the integrator needs no potential: the force kernel skips it here
   e = enqueue_force(c, c->d.active, nullptr, an, 4, jn, 4, nullptr, 0, f64, 1, 1, false,
-                    c->d.N);
+                    c->d.N, true);
   if (e != cudaSuccess) return e;
   CorrectArgs ca{};
   ca.active = c->d.active;
@@ -358,6 +362,7 @@ cudaError_t enqueue_block_step(nb_ctx* c) {
   ca.T = T;
   ca.lmin = c->cfg.level_min;
   ca.lmax = c->cfg.level_max;
+  ca.reset_tmin = 1;
   return launch_correct(c->d, ca, c->d.N, c->st);
 }
 

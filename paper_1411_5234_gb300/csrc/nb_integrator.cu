@@ -1,16 +1,19 @@
 // nb_integrator.cu -- block-time-step machinery around the force kernels.
 //
-// One block step (Sec. 2 items 1 and 2) is a fixed sequence of launches whose
-// sizes all live on the device, so it can be captured in a CUDA graph:
-//   k_tmin     t_next(k) = min_i (t_i + dt_i) per cluster          (O(N))
-//   k_predict  Taylor predictor of EVERY particle to t_next, written
-//              as the source arrays; counts due particles per block (O(N))
-//   k_scan     exclusive scan of the per-block counts (one CTA)
-//   k_scatter  active list {i : t_i + dt_i = t_next}, ascending (O(N))
-//   k_plan     per-cluster i-split factor B_k and work-item offsets
-//   force      (nb_force_mixed.cu / nb_force_fp64.cu)          O(m N)
-//   k_reduce   fixed-order sum of the B_k partials per target
-//   k_correct  Hermite corrector, step criterion, power-of-two level (O(m))
+// One block step (Sec. 2 items 1 and 2) is a fixed sequence of seven launches
+// whose sizes all live on the device, so it can be captured in a CUDA graph:
+//   k_tmin       t_next(k) = min_i (t_i + dt_i) per cluster        (O(N))
+//   k_predict    Taylor predictor of EVERY particle to t_next, written
+//                as the source arrays; counts due particles per tile (O(N))
+//   k_scan_plan  exclusive scan of the per-tile counts, each cluster's
+//                offset in the active list, and the plan: per-cluster
+//                i-split factor B_k and work-item offsets (one CTA)
+//   k_scatter    active list {i : t_i + dt_i = t_next}, ascending (O(N))
+//   force        (nb_force_mixed.cu / nb_force_fp64.cu)          O(m N)
+//   k_reduce     fixed-order sum of the B_k partials per target
+//   k_correct    Hermite corrector, step criterion, power-of-two level (O(m))
+// A force evaluation on a caller's list (nb_force) uses k_scan and k_plan
+// on their own.
 #include <cfloat>
 #include <climits>
 
@@ -204,8 +207,11 @@ __global__ void __launch_bounds__(kMixJT) k_scatter_tiles(Dev d, int T) {
 }
 
 // Work plan: per-cluster active count m_k, i-split factor B_k (Sec. 2 item 3)
-// and work-item offsets.  One CTA.
-__global__ void k_plan(Dev d, PlanArgs p) {
+// and work-item offsets.  One CTA (every thread calls it).  In step mode the
+// cluster's new block time t_min[k] becomes t_cur[k]; t_min itself is reset
+// here (reset_tmin) or, when the active list is still to be built from it,
+// by the step's corrector.
+__device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p, bool reset_tmin) {
   __shared__ unsigned long long shu[32];
   __shared__ int32_t shi[32];
   __shared__ int32_t bg_sh;
@@ -265,12 +271,12 @@ __global__ void k_plan(Dev d, PlanArgs p) {
       B = ceil_div64(Sk, chunk_len(Sk, B, p.JT));  // every chunk non-empty
       d.bfac[k] = static_cast<int32_t>(B);
       items = static_cast<int32_t>(ceil_div64(mk, p.NI) * B);
-      if (B > kReduceSerial)  // (i-tile, row segment) units of k_reduce_wide
+      if (B > kReduceSerial)  // (i-tile, row segment) units of k_reduce
         wide = static_cast<int32_t>(ceil_div64(mk, p.NI) * ceil_div64(B, kWideRows));
       if (p.step_mode) {
         const int64_t tn = d.t_min[k];
         if (tn != LLONG_MAX) d.t_cur[k] = tn;
-        d.t_min[k] = LLONG_MAX;
+        if (reset_tmin) d.t_min[k] = LLONG_MAX;
       }
     }
     int32_t tot, wtot;
@@ -289,12 +295,36 @@ __global__ void k_plan(Dev d, PlanArgs p) {
   }
 }
 
+__global__ void k_plan(Dev d, PlanArgs p) { plan_body(d, p, true); }
+
+// Block step: the scan of the per-tile due counts (k_scan), each cluster's
+// offset in the active list (the scanned count of its first tile) and the
+// plan, in one CTA of 1024 threads.  t_min stays for k_scatter_tiles; the
+// corrector resets it.
+__global__ void k_scan_plan(Dev d, int32_t nblk, PlanArgs p) {
+  __shared__ int32_t sh[32];
+  int32_t carry = 0;
+  for (int32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
+    const int32_t b = b0 + threadIdx.x;
+    const int32_t v = b < nblk ? d.blk_count[b] : 0;
+    int32_t tot;
+    const int32_t ex = block_excl_scan(v, sh, &tot);
+    if (b < nblk) d.blk_count[b] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) d.act_off[d.K] = carry;
+  __syncthreads();
+  for (int32_t k = threadIdx.x; k < d.K; k += blockDim.x) d.act_off[k] = d.blk_count[d.toff[k]];
+  __syncthreads();
+  plan_body(d, p, false);
+}
+
 // Fixed-order sum of the B_k partials of every target whose cluster was
 // split (Sec. 2 item 3); the order depends on B_k alone.
-//   k_reduce (1 < B_k <= kReduceSerial): each lane owns one target and sums
+//   1 < B_k <= kReduceSerial: each lane owns one target and sums
 //     b = 0 .. B_k - 1 in order (the lanes of a warp read consecutive targets
 //     of one partial row).
-//   k_reduce_wide (B_k > kReduceSerial: few active targets split over many
+//   B_k > kReduceSerial (few active targets split over many
 //     source chunks): the partial rows of an i-tile are cut into segments of
 //     kWideRows rows; one CTA of kWideRows warps takes one segment of one
 //     block of 32 targets, warp r holding row r, and combines the rows in
@@ -313,10 +343,17 @@ __device__ __forceinline__ void write_reduced(const ForceArgs& a, int32_t s, con
   if (a.out_pot) a.out_pot[row * a.sp] = a.G * v[6];
 }
 
-__global__ void k_reduce(ForceArgs a, int NI, int with_acc) {
-  const int32_t m = a.act_off[a.K];
+constexpr size_t kWideSmem = sizeof(double) * kPartialComps * kWideRows * 32;
+
+__global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
+                                                           int with_acc) {
+  extern __shared__ double red[];  // [component][row r][lane]
+  __shared__ int last_sh;
+  const int32_t K = a.K;
+  // small splits: one lane per target
+  const int32_t m = a.act_off[K];
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {
-    const int32_t k = upper_bound_i32(a.act_off, a.K + 1, s) - 1;
+    const int32_t k = upper_bound_i32(a.act_off, K + 1, s) - 1;
     const int32_t B = a.bfac[k];
     if (B <= 1 || B > kReduceSerial) continue;
     const int32_t local = s - a.act_off[k];
@@ -333,15 +370,7 @@ __global__ void k_reduce(ForceArgs a, int NI, int with_acc) {
     }
     write_reduced(a, s, v, with_acc);
   }
-}
-
-constexpr size_t kWideSmem = sizeof(double) * kPartialComps * kWideRows * 32;
-
-__global__ void __launch_bounds__(32 * kWideRows) k_reduce_wide(ForceArgs a, int NI,
-                                                                int with_acc) {
-  extern __shared__ double red[];  // [component][row r][lane]
-  __shared__ int last_sh;
-  const int32_t K = a.K;
+  // large splits: (i-tile, row segment, block of 32 targets) units
   const int32_t cbs = NI / 32;
   const int32_t units = a.wt_off[K] * cbs;
   const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
@@ -472,64 +501,95 @@ __device__ __forceinline__ int32_t new_level(double dt, int32_t L_old, int64_t t
 
 // Hermite corrector (Sec. 2 item 1) of the listed particles, new step level,
 // and the state write-back.
+// One active particle per group of 4 lanes: lane q < 3 takes component q of
+// the predictor and corrector, and the four norms of the step criterion are
+// summed across the group in the order (x^2 + y^2) + z^2; lane q then takes
+// the square root of norm q.  The per-lane FP64 work is about a third of a
+// particle's (GB300's FP64 pipe is the bound here).
 __global__ void k_correct(Dev d, CorrectArgs c) {
   const int64_t m = c.count_dev ? (int64_t)*c.count_dev : c.count_host;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < m;
-       s += (int64_t)gridDim.x * blockDim.x) {
+  if (c.reset_tmin && blockIdx.x == 0)  // the block step's t_min is used up
+    for (int32_t k = threadIdx.x; k < d.K; k += blockDim.x) d.t_min[k] = LLONG_MAX;
+  const int q = threadIdx.x & 3;
+  const unsigned gmask = 0xfu << (threadIdx.x & 28);
+  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
+  const int64_t gs = ((int64_t)gridDim.x * blockDim.x) >> 2;
+  for (int64_t s = g0; s < m; s += gs) {
     const int32_t i = c.active[s];
     if (i < 0 || i >= d.N) {
-      atomicOr(d.status, kStatusInval);
+      if (q == 0) atomicOr(d.status, kStatusInval);
       continue;
     }
     const int32_t cl = d.cid[i];
     const int64_t tn = c.t_tgt ? c.t_tgt[cl] : c.t_fixed;
     const int64_t ti = d.t[i];
     if (tn <= ti) {  // a step must move forward in time
-      atomicOr(d.status, kStatusInval);
+      if (q == 0) atomicOr(d.status, kStatusInval);
       continue;
     }
     const double t = ldexp((double)(tn - ti), -c.T);
-    const dbl4 p = d.pos[i], v = d.vel[i], a0 = d.acc[i], j0 = d.jerk[i];
-    double3 xp, vp;
-    predict1(p, v, a0, j0, t, xp, vp);
-    const double a1[3] = {c.acc[s * c.sa], c.acc[s * c.sa + 1], c.acc[s * c.sa + 2]};
-    const double j1[3] = {c.jerk[s * c.sj], c.jerk[s * c.sj + 1], c.jerk[s * c.sj + 2]};
-    const double a0v[3] = {a0.x, a0.y, a0.z}, j0v[3] = {j0.x, j0.y, j0.z};
-    const double xpv[3] = {xp.x, xp.y, xp.z}, vpv[3] = {vp.x, vp.y, vp.z};
-    // the Hermite fit's divisions as multiplications by 1/t^2, 1/t^3 and
-    // the Taylor coefficients (FP64 division is a long sequence here)
+    // component q of the state (q == 3: the fourth word of each record)
+    const double x0 = reinterpret_cast<const double*>(d.pos + i)[q];
+    const double v0 = reinterpret_cast<const double*>(d.vel + i)[q];
+    const double a0 = reinterpret_cast<const double*>(d.acc + i)[q];
+    const double j0 = reinterpret_cast<const double*>(d.jerk + i)[q];
+    const double a1 = q < 3 ? c.acc[s * c.sa + q] : 0.0;
+    const double j1 = q < 3 ? c.jerk[s * c.sj + q] : 0.0;
+    // Taylor predictor (Horner form), as predict1
+    const double h = 0.5 * t, th = t * (1.0 / 3.0);
+    const double xp = x0 + t * (v0 + h * (a0 + th * j0));
+    const double vp = v0 + t * (a0 + h * j0);
+    // the Hermite fit's divisions as multiplications by 1/t^2, 1/t^3 (exact
+    // powers of two in a block step) and the Taylor coefficients
     const double t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
-    // a block step's t is a power of two: its reciprocals are exact scalings
-    // (the same values the divisions give), without FP64 divisions
     int te;
     const bool pow2 = frexp(t, &te) == 0.5;
     const double it2 = pow2 ? ldexp(1.0, 2 - 2 * te) : 1.0 / t2;
     const double it3 = pow2 ? ldexp(1.0, 3 - 3 * te) : it2 / t;
     const double c24 = t4 * (1.0 / 24.0), c120 = t5 * (1.0 / 120.0), c6 = t3 * (1.0 / 6.0);
-    double x1[3], v1[3], a2e[3], a3[3];
+    const double da = a0 - a1;
+    const double a2 = (-6.0 * da - t * (4.0 * j0 + 2.0 * j1)) * it2;
+    const double a3 = (12.0 * da + 6.0 * t * (j0 + j1)) * it3;
+    const double x1 = xp + a2 * c24 + a3 * c120;
+    const double v1 = vp + a2 * c6 + a3 * c24;
+    const double a2e = a2 + a3 * t;
+    // squared norms over the group: lanes (0 + 1) then + 2 (lane 3 adds 0)
+    double n[4];
+    n[0] = q < 3 ? a1 * a1 : 0.0;
+    n[1] = q < 3 ? j1 * j1 : 0.0;
+    n[2] = q < 3 ? a2e * a2e : 0.0;
+    n[3] = q < 3 ? a3 * a3 : 0.0;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const double da = a0v[q] - a1[q];
-      const double a2 = (-6.0 * da - t * (4.0 * j0v[q] + 2.0 * j1[q])) * it2;
-      a3[q] = (12.0 * da + 6.0 * t * (j0v[q] + j1[q])) * it3;
-      x1[q] = xpv[q] + a2 * c24 + a3[q] * c120;
-      v1[q] = vpv[q] + a2 * c6 + a3[q] * c24;
-      a2e[q] = a2 + a3[q] * t;
+    for (int k = 0; k < 4; ++k) {
+      n[k] += __shfl_xor_sync(gmask, n[k], 1, 4);
+      n[k] += __shfl_xor_sync(gmask, n[k], 2, 4);
     }
-    const double dt = aarseth(norm3(a1[0], a1[1], a1[2]), norm3(j1[0], j1[1], j1[2]),
-                              norm3(a2e[0], a2e[1], a2e[2]), norm3(a3[0], a3[1], a3[2]), c.eta);
+    // lane q takes sqrt of norm q; gather the four
+    const double mine = sqrt(q == 0 ? n[0] : q == 1 ? n[1] : q == 2 ? n[2] : n[3]);
+    const double na = __shfl_sync(gmask, mine, 0, 4), nj = __shfl_sync(gmask, mine, 1, 4);
+    const double n2 = __shfl_sync(gmask, mine, 2, 4), n3 = __shfl_sync(gmask, mine, 3, 4);
+    const double dt = aarseth(na, nj, n2, n3, c.eta);
     const int32_t L = new_level(dt, d.level[i], tn, c.T, c.lmin, c.lmax);
-    bool finite = true;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) finite = finite && isfinite(x1[q]) && isfinite(v1[q]);
-    if (!finite) atomicOr(d.status, kStatusNonFinite);
-    const double pot = c.pot ? c.pot[s * c.sp] : a0.w;
-    d.pos[i] = dbl4{x1[0], x1[1], x1[2], p.w};
-    d.vel[i] = dbl4{v1[0], v1[1], v1[2], 0.0};
-    d.acc[i] = dbl4{a1[0], a1[1], a1[2], pot};
-    d.jerk[i] = dbl4{j1[0], j1[1], j1[2], 0.0};
-    d.t[i] = tn;
-    d.level[i] = L;
+    const bool bad = q < 3 && !(isfinite(x1) && isfinite(v1));
+    if (__any_sync(gmask, bad) && q == 0) atomicOr(d.status, kStatusNonFinite);
+    double* P = reinterpret_cast<double*>(d.pos + i);
+    double* V = reinterpret_cast<double*>(d.vel + i);
+    double* A = reinterpret_cast<double*>(d.acc + i);
+    double* J = reinterpret_cast<double*>(d.jerk + i);
+    if (q < 3) {
+      P[q] = x1;
+      V[q] = v1;
+      A[q] = a1;
+      J[q] = j1;
+    } else {  // the fourth words: mass kept, potential from this step when given
+      V[3] = 0.0;
+      if (c.pot) A[3] = c.pot[s * c.sp];
+      J[3] = 0.0;
+    }
+    if (q == 0) {
+      d.t[i] = tn;
+      d.level[i] = L;
+    }
   }
 }
 
@@ -687,8 +747,8 @@ cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, 
                                                                   f64, count_due);
   return cudaGetLastError();
 }
-cudaError_t launch_compact(const Dev& d, int T, cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(d, static_cast<int32_t>(d.n_tiles));
+cudaError_t launch_scan_plan_scatter(const Dev& d, const PlanArgs& p, int T, cudaStream_t st) {
+  k_scan_plan<<<1, 1024, 0, st>>>(d, static_cast<int32_t>(d.n_tiles), p);
   k_scatter_tiles<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d, T);
   return cudaGetLastError();
 }
@@ -697,22 +757,21 @@ cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
-                          int wide_grid, cudaStream_t st) {
-  // one lane per target for small splits; the wide kernel for large ones
-  // (both exit at once when the plan gave them nothing to do)
-  k_reduce<<<blocks_for(m_bound, 256), 256, 0, st>>>(a, NI, with_acc ? 1 : 0);
-  k_reduce_wide<<<wide_grid > 0 ? wide_grid : 1, 32 * kWideRows, kWideSmem, st>>>(
-      a, NI, with_acc ? 1 : 0);
+                          int grid, cudaStream_t st) {
+  // one persistent CTA of 1024 threads per SM (its 57 KB of shared memory
+  // serve the large splits); exits at once when the plan split nothing
+  (void)m_bound;
+  k_reduce<<<grid > 0 ? grid : 1, 32 * kWideRows, kWideSmem, st>>>(a, NI, with_acc ? 1 : 0);
   return cudaGetLastError();
 }
 cudaError_t integrator_setup() {
-  return cudaFuncSetAttribute(k_reduce_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(kWideSmem));
 }
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {
-  // 32-thread CTAs: a few hundred active particles still spread over many
-  // SMs (the corrector is FP64 arithmetic, ~2 lanes per SM per clock)
-  k_correct<<<blocks_for(m_bound, 32), 32, 0, st>>>(d, c);
+  // 4 lanes per particle in 32-thread CTAs: a few hundred active particles
+  // still spread over many SMs (FP64 arithmetic, ~2 lanes per SM per clock)
+  k_correct<<<blocks_for(4 * m_bound, 32), 32, 0, st>>>(d, c);
   return cudaGetLastError();
 }
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,

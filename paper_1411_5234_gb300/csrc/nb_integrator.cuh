@@ -123,18 +123,20 @@ struct CorrectArgs {
   int64_t t_fixed;
   double eta;
   int T, lmin, lmax;
+  int reset_tmin;             // block step: reset the clusters' t_min (used up)
 };
 
 cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t st);
 cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st);
 cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T, bool mix,
                            bool f64, bool count_due, cudaStream_t st);
-cudaError_t launch_compact(const Dev& d, int T, cudaStream_t st);
+// block step: scan + plan (one CTA), then the active list
+cudaError_t launch_scan_plan_scatter(const Dev& d, const PlanArgs& p, int T, cudaStream_t st);
 cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st);
-// wide_grid: CTAs of the wide-split reduction (one per SM is enough)
+// grid: persistent CTAs of the reduction (one per SM)
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
-                          int wide_grid, cudaStream_t st);
-// one-time kernel attributes (the wide reduction's dynamic shared memory)
+                          int grid, cudaStream_t st);
+// one-time kernel attributes (the reduction's dynamic shared memory)
 cudaError_t integrator_setup();
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st);
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,
