@@ -273,12 +273,12 @@ def random_active(n: int, m: int, seed: int = 0) -> np.ndarray:
     return np.sort(pick).astype(np.int32)
 
 
-def random_vectors(n: int, scale: float, seed: int = 0) -> np.ndarray:
-    """n isotropic vectors with lengths uniform in [0, scale) (n x 3 float64):
+def random_vectors(n: int, scale: float, seed: int = 0, lo: float = 0.0) -> np.ndarray:
+    """n isotropic vectors with lengths uniform in [lo, scale) (n x 3 float64):
     synthetic stand-ins for state a test sets directly (e.g. the acceleration
     and jerk at the start of a step)."""
     st = Stream(seed, 7)
-    return _isotropic(st, n) * (scale * st.uniform(n))[:, None]
+    return _isotropic(st, n) * (lo + (scale - lo) * st.uniform(n))[:, None]
 
 
 def morton_order(pos: np.ndarray, bits: int = 21) -> np.ndarray:

@@ -122,3 +122,108 @@ def test_full_size_fp64_force_sampled(nb, cluster):
     assert rel_err(acc, ra).max() <= 1e-12
     assert rel_err(jerk, rj).max() <= 1e-12
     assert np.abs(pot / rp - 1).max() <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# One block step of individual (power-of-two) time steps at the full sizes of
+# the other integration workloads, in the launch configuration bench.py uses
+# for them (mixed, autotuned shape, graphs of 16 steps).  Start: the initial
+# state plus seeded synthetic a0, j0 (|a0| uniform in [0.05, 2), |j0| = 20),
+# levels from the step criterion's start rule, every t = 0.  The oracle
+# predicts every particle to its cluster's next block time and computes the
+# force, corrector and new level of sampled due particles one by one; sampled
+# particles that are not due must come back unchanged.
+
+def _integration_case(name):
+    if name == "plummer65536":
+        cl = inputs.plummer(65536, seed=0)
+        return cl, 1e-4, 20
+    if name == "binaries262144":
+        return inputs.plummer_binaries(262144, seed=0), 1e-5, 30
+    cl = inputs.plummer_batch(512, 256, 16384, seed0=0)
+    return cl, 1e-4, 30
+
+
+@pytest.mark.parametrize("name", ["plummer65536", "batch512", "binaries262144"])
+def test_full_size_individual_block_step_sampled(nb, name):
+    cl, eps, lmax = _integration_case(name)
+    n, T, lmin, eta = cl.n, 40, 3, 0.01
+    off = cl.offsets
+    a0 = inputs.random_vectors(n, 2.0, seed=21, lo=0.05)
+    j0 = inputs.random_vectors(n, 20.0, seed=22, lo=20.0 - 1e-12)
+    lev0 = np.array([oracle.level(oracle.initial_dt(a0[i], j0[i], 0.01), -1, 0, T, lmin, lmax)
+                     for i in range(n)], dtype=np.int32)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, offsets=off, eps=eps, precision=nb.NB_MIXED,
+                 level_min=lmin, level_max=lmax, graph_steps=16)
+    try:
+        sim.autotune()
+        sim.set_state(cl.pos, cl.vel, a0, j0, np.zeros(n, dtype=np.int64), lev0)
+        sim.step(1)
+        s = sim.get_state()
+        assert sim.status() == nb.NB_OK
+    finally:
+        sim.close()
+
+    # next block time of each cluster: its finest occupied level
+    cid = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    lmax_k = np.full(len(off) - 1, -1)
+    np.maximum.at(lmax_k, cid, lev0)
+    t_next = (np.int64(1) << (T - lmax_k)).astype(np.int64)
+    due = lev0 == lmax_k[cid]
+    tau = np.ldexp(t_next[cid].astype(np.float64), -T)
+
+    rng_due = np.flatnonzero(due)
+    rng_idle = np.flatnonzero(~due)
+    pick = inputs.random_active(len(rng_due), min(128, len(rng_due)), seed=31)
+    sample = rng_due[pick]
+    idle = rng_idle[inputs.random_active(len(rng_idle), 64, seed=32)]
+
+    # not due: untouched
+    for key, ref in (("pos", cl.pos), ("vel", cl.vel), ("acc", a0), ("jerk", j0)):
+        assert np.array_equal(s[key][idle], ref[idle]), key
+    assert np.all(s["t"][idle] == 0) and np.array_equal(s["level"][idle], lev0[idle])
+
+    # due: force at the predicted positions, corrector, level
+    xp, vp = oracle.predict(cl.pos, cl.vel, a0, j0, tau)
+    ra = np.empty((len(sample), 3))
+    rj = np.empty((len(sample), 3))
+    Sa = np.empty(len(sample))
+    Sj = np.empty(len(sample))
+    for k in np.unique(cid[sample]):
+        lo_, hi_ = off[k], off[k + 1]
+        rows = np.flatnonzero(cid[sample] == k)
+        loc = sample[rows] - lo_
+        a_, j_, _ = oracle.force(xp[lo_:hi_], vp[lo_:hi_], cl.mass[lo_:hi_], eps,
+                                 idx=loc.astype(np.int64))
+        ra[rows], rj[rows] = a_, j_
+        Sa[rows], Sj[rows] = term_sums_big(xp[lo_:hi_], vp[lo_:hi_], cl.mass[lo_:hi_], eps, loc)
+    check_mixed(s["acc"][sample], s["jerk"][sample], ra, rj, Sa, Sj)
+
+    tau_s = tau[sample]
+    x1, v1, a2e, a3 = oracle.correct(tau_s, xp[sample], vp[sample], a0[sample], j0[sample],
+                                     ra, rj)
+    nrm = lambda v: np.linalg.norm(v, axis=1)
+    da = nrm(s["acc"][sample] - ra)
+    dj = nrm(s["jerk"][sample] - rj)
+    amag = nrm(a0[sample]) + nrm(ra)
+    jmag = nrm(j0[sample]) + nrm(rj)
+    taylor_x = (nrm(cl.pos[sample]) + nrm(cl.vel[sample]) * tau_s + amag * tau_s ** 2
+                + jmag * tau_s ** 3)
+    taylor_v = nrm(cl.vel[sample]) + amag * tau_s + jmag * tau_s ** 2
+    tol_x = 1.01 * (0.15 * tau_s ** 2 * da + tau_s ** 3 / 30 * dj) + 8e-16 * taylor_x
+    tol_v = 1.01 * (0.5 * tau_s * da + tau_s ** 2 / 12 * dj) + 8e-16 * taylor_v
+    assert np.all(nrm(s["pos"][sample] - x1) <= tol_x)
+    assert np.all(nrm(s["vel"][sample] - v1) <= tol_v)
+    assert np.array_equal(s["t"][sample], t_next[cid[sample]])
+    # level: the oracle's rule on the oracle's force.  The GPU decides on its
+    # own (mixed) force, so where the criterion lies within 2^-14 (relative)
+    # of a power of two the level may differ by one; elsewhere it is exact.
+    dtc = np.array([oracle.aarseth_dt(ra[r], rj[r], a2e[r], a3[r], eta)
+                    for r in range(len(sample))])
+    lev_ref = np.array([oracle.level(dtc[r], lev0[i], int(t_next[cid[i]]), T, lmin, lmax)
+                        for r, i in enumerate(sample)])
+    e = np.log2(dtc)
+    near_edge = np.abs(e - np.round(e)) < 2.0 ** -14 / np.log(2.0)
+    got = s["level"][sample]
+    assert np.array_equal(got[~near_edge], lev_ref[~near_edge])
+    assert np.all(np.abs(got[near_edge] - lev_ref[near_edge]) <= 1)
