@@ -42,6 +42,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_INTERACTION = 38          # acceleration + jerk convention
+FLOPS_PER_INTERACTION_ACC = 20      # acceleration-only convention
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 METRIC = "pair-interactions/s (and % FP32 peak) at N=2^20, mixed vs FP64, at stated error"
 KERNEL_FILES = [os.path.join(ROOT, "paper_1411_5234_gb300", "csrc", f)
@@ -62,7 +63,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="skip nb_autotune before timing")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--kernel-case", choices=["mixed", "fp64"], default=None,
+    p.add_argument("--kernel-case", choices=["mixed", "fp64", "mixed-acc"], default=None,
                    help="run only nb_force on m random targets of N (profiling case)")
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--variant", type=int, default=None, help="mixed force kernel shape")
@@ -195,20 +196,22 @@ def kernel_case(args):
     from paper_1411_5234_gb300 import inputs, nbody
     torch.cuda.set_device(0)
     cl = make_cluster(args.n, 0)
-    prec = nbody.NB_MIXED if args.kernel_case == "mixed" else nbody.NB_FP64
+    prec = nbody.NB_FP64 if args.kernel_case == "fp64" else nbody.NB_MIXED
+    want_jerk = args.kernel_case != "mixed-acc"
+    flops = FLOPS_PER_INTERACTION if want_jerk else FLOPS_PER_INTERACTION_ACC
     kw = {} if args.variant is None else {"variant": args.variant}
     sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=prec, graph_steps=0, **kw)
     sim.predict(0)
     act = torch.as_tensor(inputs.random_active(cl.n, args.m, seed=1), device="cuda")
     acc = torch.empty((args.m, 3), dtype=torch.float64, device="cuda")
-    jerk = torch.empty_like(acc)
+    jerk = torch.empty_like(acc) if want_jerk else None
     for _ in range(args.warmup):
-        sim.force(act, acc, jerk, None, want_pot=False)
+        sim.force(act, acc, jerk, None, want_pot=False, want_jerk=want_jerk)
     sim.synchronize()
     wt0, nt0 = sim.tile_stats()
     sim.profile(True)
     for _ in range(args.steps):
-        sim.force(act, acc, jerk, None, want_pot=False)
+        sim.force(act, acc, jerk, None, want_pot=False, want_jerk=want_jerk)
     ms, cnt = sim.profile_read()
     assert sim.status() == nbody.NB_OK
     per = ms / max(cnt, 1)
@@ -218,7 +221,8 @@ def kernel_case(args):
                       "near_tile_share": (nt - nt0) / max(wt - wt0, 1),
                       "N": cl.n, "m": args.m,
                       "ms_per_launch": per, "interactions_per_s": rate,
-                      "frac_fp32_peak_38": FLOPS_PER_INTERACTION * rate
+                      "flops_per_interaction": flops,
+                      "frac_fp32_peak": flops * rate
                       / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6)}), flush=True)
     sim.close()
     return 0
@@ -566,6 +570,27 @@ def sweep(nbody, inputs, torch, cl):
                 entry["frac_fp32_peak"] = (FLOPS_PER_INTERACTION * rate
                                            / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6))
             out[name].append(entry)
+    # acceleration only (nb_force with jerk == NULL), 20 flops per interaction
+    out["mixed_acc_only"] = []
+    s = sims["mixed"]
+    for k in (10, 6, 0):
+        m = n >> k
+        act = torch.as_tensor(inputs.random_active(n, m, seed=k), device="cuda")
+        acc = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+        s.force(act, acc, None, None, want_pot=False, want_jerk=False)
+        s.synchronize()
+        s.profile_read()
+        best = math.inf
+        for _ in range(3):
+            s.force(act, acc, None, None, want_pot=False, want_jerk=False)
+            ms, cnt = s.profile_read()
+            best = min(best, ms / max(cnt, 1))
+        rate = m * n / (best * 1e-3)
+        out["mixed_acc_only"].append({
+            "active_fraction": f"2^-{k}", "m": m, "interactions_per_s": rate, "ms": best,
+            "flops_per_interaction": FLOPS_PER_INTERACTION_ACC,
+            "frac_fp32_peak": (FLOPS_PER_INTERACTION_ACC * rate
+                               / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6))})
     # accuracy: mixed vs FP64 on 4096 targets (GPU against GPU; the oracle
     # checks both paths at this size in tests/test_gpu_full_size.py)
     idx = inputs.random_active(n, 4096, seed=123)
@@ -575,15 +600,20 @@ def sweep(nbody, inputs, torch, cl):
         a, j, p = sims[name].force(act)
         sims[name].synchronize()
         res[name] = (a.cpu().numpy(), j.cpu().numpy(), p.cpu().numpy())
+    a_acc, _, _ = sims["mixed"].force(act, want_jerk=False)
+    sims["mixed"].synchronize()
     rel = lambda x, r: np.linalg.norm(x - r, axis=1) / np.linalg.norm(r, axis=1)
     ea, ej = rel(res["mixed"][0], res["fp64"][0]), rel(res["mixed"][1], res["fp64"][1])
     ep = np.abs(res["mixed"][2] / res["fp64"][2] - 1)
+    eaa = rel(a_acc.cpu().numpy(), res["fp64"][0])
     out["accuracy"] = {
         "mixed_vs_fp64_4096_targets": {
             "acc_rel_max": float(ea.max()), "acc_rel_median": float(np.median(ea)),
             "acc_rel_p999": float(np.quantile(ea, 0.999)),
             "jerk_rel_max": float(ej.max()), "jerk_rel_median": float(np.median(ej)),
-            "pot_rel_max": float(ep.max())}}
+            "pot_rel_max": float(ep.max())},
+        "mixed_acc_only_vs_fp64_4096_targets": {
+            "acc_rel_max": float(eaa.max()), "acc_rel_median": float(np.median(eaa))}}
     mx = {e["m"]: e["interactions_per_s"] for e in out["mixed"]}
     out["mixed_over_fp64_speedup"] = {e["active_fraction"]: mx[e["m"]] / e["interactions_per_s"]
                                       for e in out["fp64"]}

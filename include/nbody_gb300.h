@@ -130,12 +130,16 @@ int nb_predict(nb_ctx *ctx, int64_t t_ticks);
 /* Acceleration, jerk and potential (Eq. 1, Eq. 2) of the m particles listed in
  * active_idx (device int32, m entries, global particle indices in any order,
  * no repeats) from the predicted sources of their own cluster (the last
- * nb_predict).  acc and jerk: device (m x 3) doubles; pot: device m doubles
- * or NULL.  Row k of the outputs belongs to active_idx[k].  The targets are
- * evaluated in the library's spatial source order and written back to their
- * rows.  m == 0 is a no-op.  Asynchronous; an out-of-range or repeated entry
- * sets the sticky status to NB_EINVAL and the rows of the offending entries
- * are left unwritten. */
+ * nb_predict).  acc: device (m x 3) doubles; jerk: device (m x 3) doubles or
+ * NULL; pot: device m doubles or NULL.  With jerk == NULL only the
+ * acceleration (and the potential) is wanted: a mixed-precision context
+ * then runs a kernel without the velocity terms (about half the arithmetic
+ * per interaction, for acceleration-only integrators such as leapfrog); an
+ * FP64 context computes the jerk and drops it.  Row k of the outputs belongs
+ * to active_idx[k].  The targets are evaluated in the library's spatial
+ * source order and written back to their rows.  m == 0 is a no-op.
+ * Asynchronous; an out-of-range or repeated entry sets the sticky status to
+ * NB_EINVAL and the rows of the offending entries are left unwritten. */
 int nb_force(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
              double *jerk, double *pot);
 

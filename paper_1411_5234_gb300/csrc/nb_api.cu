@@ -183,7 +183,7 @@ struct nb_ctx {
   Dev d;
   Layout L{};
   cudaStream_t st = nullptr;
-  int grid_mix = 0, grid_f64 = 0, sms = 0;
+  int grid_mix = 0, grid_f64 = 0, grid_acc = 0, sms = 0;
   std::vector<int64_t> off_host;
   std::vector<double> mass_host;
   std::vector<int32_t> sperm_host;  // source slot order (for the autotuner's target lists)
@@ -245,11 +245,11 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, doub
   return a;
 }
 
-PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count) {
+PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count, bool acc_only = false) {
   PlanArgs p{};
-  p.NI = f64 ? kF64NI : force_mixed_ni(c->cfg.variant);
+  p.NI = f64 ? kF64NI : acc_only ? force_mixed_acc_ni() : force_mixed_ni(c->cfg.variant);
   p.JT = f64 ? kF64JT : kMixJT;
-  p.grid = f64 ? c->grid_f64 : c->grid_mix;
+  p.grid = f64 ? c->grid_f64 : acc_only ? c->grid_acc : c->grid_mix;
   p.forced_b = c->cfg.bfactor;
   p.part_items = c->L.part_items;
   p.step_mode = step_mode;
@@ -307,8 +307,11 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
                           int step_mode, int count, bool pot_only, int64_t m_bound,
                           bool planned = false) {
   cudaError_t e = cudaSuccess;
+  // no jerk wanted (and not the FP64 energy pass): the mixed path runs the
+  // acceleration-only kernel
+  const bool acc_only = !f64 && jerk == nullptr;
   if (!planned) {
-    e = launch_plan(c->d, plan_args(c, f64, step_mode, count), c->st);
+    e = launch_plan(c->d, plan_args(c, f64, step_mode, count, acc_only), c->st);
     if (e != cudaSuccess) return e;
   }
   ForceArgs fa = force_args(c, active, rows, acc, sa, jerk, sj, pot, sp, f64);
@@ -321,6 +324,8 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
   }
   if (f64)
     e = launch_force_fp64(fa, c->grid_f64, pot_only ? kF64PotOnly : kF64Full, c->st);
+  else if (acc_only)
+    e = launch_force_mixed_acc(fa, c->grid_acc, pot != nullptr, c->st);
   else
     e = launch_force_mixed(fa, c->grid_mix, pot != nullptr, c->cfg.variant, c->st);
   if (e != cudaSuccess) return e;
@@ -329,8 +334,8 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
     if (e != cudaSuccess) return e;
     c->ev_pending.push_back(ev);
   }
-  return launch_reduce(fa, f64 ? kF64NI : force_mixed_ni(c->cfg.variant), !pot_only, m_bound,
-                       c->sms, c->st);
+  const int ni = f64 ? kF64NI : acc_only ? force_mixed_acc_ni() : force_mixed_ni(c->cfg.variant);
+  return launch_reduce(fa, ni, !pot_only, m_bound, c->sms, c->st);
 }
 
 cudaError_t enqueue_block_step(nb_ctx* c) {
@@ -493,6 +498,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   }
   c->grid_mix = sms * force_mixed_ctas_per_sm(cfg->variant);
   c->grid_f64 = sms * force_fp64_ctas_per_sm();
+  c->grid_acc = sms * force_mixed_acc_ctas_per_sm();
   c->sms = sms;
   if (integrator_setup() != cudaSuccess) {
     delete c;
@@ -590,7 +596,7 @@ int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, doubl
              double* pot) {
   if (!c || m < 0 || m > c->d.N) return NB_EINVAL;
   if (m == 0) return NB_OK;
-  if (!active_idx || !acc || !jerk) return NB_EINVAL;
+  if (!active_idx || !acc) return NB_EINVAL;
   const bool f64 = !is_mixed(c);
   // targets in source-slot order (spatially coherent warps), rows mapped back
   NB_TRY(launch_list_to_slots(c->d, active_idx, m, c->st));

@@ -9,6 +9,7 @@
 //   3: 256 threads x 1 target,  totals in registers, 1/s^2 from the SFU
 //   4:  64 threads x 3 targets, totals in shared memory, 1/s^2 = rsqrt^2
 //   5:  32 threads x 4 targets (one warp per CTA), shared-memory totals
+// and, for nb_force calls that want no jerk, one acceleration-only shape.
 #include "../../include/nbody_gb300.h"
 #include "nb_force_mixed.cuh"
 
@@ -20,6 +21,10 @@ template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 1, 4>;
 template <bool POT> using S3 = mixk::MixShape<256, 1, POT, true, false, 4, 2>;
 template <bool POT> using S4 = mixk::MixShape<64, 3, POT, false, true, 1, 5>;
 template <bool POT> using S5 = mixk::MixShape<32, 4, POT, false, true, 1, 8>;
+// acceleration (and potential) only: 64 x 4 at 6 CTAs per SM was the fastest
+// of the 64x4 (5 or 6 CTAs/SM, unrolled or not), 128x2 and 256x1 shapes at
+// N = m = 2^20 (measured on GB300)
+template <bool POT> using SA = mixk::MixShape<64, 4, POT, false, true, 1, 6, false>;
 
 template <class Sh>
 cudaError_t launch_shape(const ForceArgs& a, int grid, cudaStream_t st) {
@@ -76,6 +81,12 @@ int force_mixed_ctas_per_sm(int variant) {
     case 5: return occupancy_both<S5>();
     default: return occupancy_both<S0>();
   }
+}
+
+int force_mixed_acc_ni() { return SA<false>::NI; }
+int force_mixed_acc_ctas_per_sm() { return occupancy_both<SA>(); }
+cudaError_t launch_force_mixed_acc(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st) {
+  return with_pot ? launch_shape<SA<true>>(a, grid, st) : launch_shape<SA<false>>(a, grid, st);
 }
 
 size_t force_mixed_smem() { return sizeof(float4) * 2 * mixk::kTileF4; }

@@ -48,7 +48,9 @@
 // (NT * IPT <= kMixNI targets per work item), POT computes the potential, RCP takes 1/s^2 from the
 // SFU reciprocal instead of an FP32 multiply, SMT keeps the compensated
 // totals in shared memory instead of registers, UNR unrolls the source loop,
-// MINB is the CTAs-per-SM hint of __launch_bounds__.
+// MINB is the CTAs-per-SM hint of __launch_bounds__, JERK false computes the
+// acceleration (and potential) alone: no velocities, 12 f32x2 instructions
+// per two interactions instead of 26 (for acceleration-only integrators).
 #pragma once
 #include "nb_internal.cuh"
 
@@ -67,10 +69,11 @@ constexpr float kFarRatio2 = 4.0f;
 // component order inside a group of 4 sources (float4 index)
 enum { cDXH = 0, cDYH, cDZH, cM, cVX, cVY, cVZ, cDXL, cDYL, cDZL };
 
-template <int NT_, int IPT_, bool POT_, bool RCP_, bool SMT_, int UNR_, int MINB_>
+template <int NT_, int IPT_, bool POT_, bool RCP_, bool SMT_, int UNR_, int MINB_,
+          bool JERK_ = true>
 struct MixShape {
   static constexpr int NT = NT_, IPT = IPT_, NI = NT_ * IPT_, UNR = UNR_, MINB = MINB_;
-  static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_;
+  static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_, JERK = JERK_;
   static_assert(NT_ * IPT_ <= kMixNI, "partial-sum rows hold at most kMixNI targets");
 };
 
@@ -124,9 +127,6 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
   f2 r2 = f2_fma(dx, dx, eps2);
   r2 = f2_fma(dy, dy, r2);
   r2 = f2_fma(dz, dz, r2);
-  f2 rv = f2_mul(dx, wx);
-  rv = f2_fma(dy, wy, rv);
-  rv = f2_fma(dz, wz, rv);
   f2 rinv = f2_rsqrt(r2);
   f2 rr = Sh::RCP ? f2_rcp(r2) : 0ull;
   if (MASK) {  // j == i is excluded by index (Eq. 1)
@@ -140,13 +140,18 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
   const f2 mri = f2_mul(m, rinv);
   const f2 mr3 = f2_mul(mri, r2inv);
   if (Sh::POT) s.pt = f2_add(s.pt, mri);
-  const f2 t = f2_mul(f2_mul(rv, r2inv), f2_pack(-3.f, -3.f));  // -3 d.w / s^2
   s.ax = f2_fma(mr3, dx, s.ax);
   s.ay = f2_fma(mr3, dy, s.ay);
   s.az = f2_fma(mr3, dz, s.az);
-  s.jx = f2_fma(mr3, f2_fma(t, dx, wx), s.jx);
-  s.jy = f2_fma(mr3, f2_fma(t, dy, wy), s.jy);
-  s.jz = f2_fma(mr3, f2_fma(t, dz, wz), s.jz);
+  if constexpr (Sh::JERK) {
+    f2 rv = f2_mul(dx, wx);
+    rv = f2_fma(dy, wy, rv);
+    rv = f2_fma(dz, wz, rv);
+    const f2 t = f2_mul(f2_mul(rv, r2inv), f2_pack(-3.f, -3.f));  // -3 d.w / s^2
+    s.jx = f2_fma(mr3, f2_fma(t, dx, wx), s.jx);
+    s.jy = f2_fma(mr3, f2_fma(t, dy, wy), s.jy);
+    s.jz = f2_fma(mr3, f2_fma(t, dz, wz), s.jz);
+  }
 }
 
 // Far cell: d = dh_j + eh.  NG > 0: a full cell with a compile-time trip
@@ -256,7 +261,15 @@ __device__ __forceinline__ f2 lanes_sum2(f2& a, f2& b) {
 
 template <class Sh>
 __device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT>& T, float* col) {
-  if constexpr (Sh::SMT) {  // packed two-sums, two components at a time
+  if constexpr (!Sh::JERK) {  // acceleration (and potential) only
+    if constexpr (Sh::SMT) {
+      T.add2(col, 0, lanes_sum2(s.ax, s.ay));
+    } else {
+      T.add(col, 0, lanes_sum(s.ax));
+      T.add(col, 1, lanes_sum(s.ay));
+    }
+    T.add(col, 2, lanes_sum(s.az));
+  } else if constexpr (Sh::SMT) {  // packed two-sums, two components at a time
     T.add2(col, 0, lanes_sum2(s.ax, s.ay));
     T.add2(col, 2, lanes_sum2(s.az, s.jx));
     T.add2(col, 4, lanes_sum2(s.jy, s.jz));
@@ -470,16 +483,17 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       v[0] = tot[r].get(col, 0);
       v[1] = tot[r].get(col, 1);
       v[2] = tot[r].get(col, 2);
-      v[3] = tot[r].get(col, 3);
-      v[4] = tot[r].get(col, 4);
-      v[5] = tot[r].get(col, 5);
+      v[3] = Sh::JERK ? tot[r].get(col, 3) : 0.0;
+      v[4] = Sh::JERK ? tot[r].get(col, 4) : 0.0;
+      v[5] = Sh::JERK ? tot[r].get(col, 5) : 0.0;
       v[6] = Sh::POT ? -tot[r].get(col, 6) : 0.0;
       const int32_t ql = wp * 32 * IPT + r * 32 + ln;
       if (B == 1) {
         int64_t srow = a0 + it * NI + ql;
         if (a.rows) srow = a.rows[srow];
         if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[srow * a.sa + c] = a.G * v[c];
-        if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[srow * a.sj + c] = a.G * v[3 + c];
+        if (Sh::JERK && a.out_jerk)
+          for (int c = 0; c < 3; ++c) a.out_jerk[srow * a.sj + c] = a.G * v[3 + c];
         if (Sh::POT && a.out_pot) a.out_pot[srow * a.sp] = a.G * v[6];
       } else {
         double* P = a.partials + (size_t)w * kPartialComps * NI + ql;

@@ -270,6 +270,10 @@ cudaError_t launch_force_fp64(const ForceArgs& a, int grid, int mode, cudaStream
 int force_mixed_variants();
 int force_mixed_ni(int variant);  // targets per work item of a mixed shape
 int force_mixed_ctas_per_sm(int variant);
+// the acceleration-only mixed kernel (no velocities, no jerk)
+cudaError_t launch_force_mixed_acc(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st);
+int force_mixed_acc_ni();
+int force_mixed_acc_ctas_per_sm();
 int force_fp64_ctas_per_sm();
 size_t force_mixed_smem();
 size_t force_fp64_smem();

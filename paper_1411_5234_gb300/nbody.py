@@ -199,14 +199,16 @@ class Sim:
 
     def force(self, active: torch.Tensor, acc: torch.Tensor | None = None,
               jerk: torch.Tensor | None = None, pot: torch.Tensor | None = None,
-              want_pot: bool = True):
-        """Forces on ``active`` (int32 CUDA tensor, ascending) from the last prediction."""
+              want_pot: bool = True, want_jerk: bool = True):
+        """Forces on ``active`` (int32 CUDA tensor) from the last prediction.
+        ``want_jerk=False`` asks for the acceleration (and potential) only
+        (nb_force with jerk == NULL); the returned jerk is then None."""
         if active.dtype != torch.int32 or not active.is_cuda or not active.is_contiguous():
             raise ValueError("active must be a contiguous int32 CUDA tensor")
         m = active.numel()
         if acc is None:
             acc = torch.empty((m, 3), dtype=torch.float64, device="cuda")
-        if jerk is None:
+        if jerk is None and want_jerk:
             jerk = torch.empty((m, 3), dtype=torch.float64, device="cuda")
         if pot is None and want_pot:
             pot = torch.empty(m, dtype=torch.float64, device="cuda")

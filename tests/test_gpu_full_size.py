@@ -227,3 +227,25 @@ def test_full_size_individual_block_step_sampled(nb, name):
     got = s["level"][sample]
     assert np.array_equal(got[~near_edge], lev_ref[~near_edge])
     assert np.all(np.abs(got[near_edge] - lev_ref[near_edge]) <= 1)
+
+
+def test_full_size_acceleration_only_sampled(nb, cluster):
+    """Acceleration-only mixed kernel at N = 2^20 on 1024 random targets."""
+    cl = cluster
+    idx = inputs.random_active(N, 1024, seed=6)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=EPS, precision=nb.NB_MIXED)
+    try:
+        sim.predict(0)
+        acc, jerk, pot = sim.force(torch.as_tensor(idx, device="cuda"), want_jerk=False)
+        torch.cuda.synchronize()
+        assert jerk is None and sim.status() == nb.NB_OK
+        acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
+    finally:
+        sim.close()
+    ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, EPS, idx=idx.astype(np.int64))
+    sub = np.arange(0, 1024, 8)
+    Sa, _ = term_sums_big(cl.pos, cl.vel, cl.mass, EPS, idx[sub])
+    assert (np.linalg.norm(acc[sub] - ra[sub], axis=1) / Sa).max() <= 1e-6
+    ea = rel_err(acc, ra)
+    assert np.median(ea) <= 1e-7 and np.quantile(ea, 0.999) <= 1e-6
+    assert np.abs(pot / rp - 1).max() <= 1e-6

@@ -401,3 +401,42 @@ def test_autotune_picks_a_shape_and_keeps_results(nb):
     sim.step(9)                                   # graphs rebuilt with the chosen shape
     assert sim.status() == nb.NB_OK
     sim.close()
+
+
+# ------------------------------------------------- acceleration only ----
+
+@pytest.mark.parametrize("n,m", [(4099, "all"), (20000, 999)])
+def test_mixed_acceleration_only_parity(nb, n, m):
+    """nb_force with jerk == NULL runs the kernel without velocity terms:
+    acceleration and potential against the oracle with the mixed gates."""
+    cl = inputs.plummer(n, seed=3, imf="kroupa")
+    idx = np.arange(n) if m == "all" else inputs.random_active(n, m, seed=4)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nb.NB_MIXED)
+    sim.predict(0)
+    act = torch.as_tensor(np.asarray(idx, dtype=np.int32), device="cuda")
+    acc, jerk, pot = sim.force(act, want_jerk=False)
+    torch.cuda.synchronize()
+    assert jerk is None and sim.status() == nb.NB_OK
+    acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
+    sim.close()
+    ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=np.asarray(idx, dtype=np.int64))
+    Sa, Sj = term_sums(cl, 1e-4, idx)
+    ca = np.linalg.norm(acc - ra, axis=1) / Sa
+    assert ca.max() <= 1e-6, ca.max()
+    ea = rel_err(acc, ra)
+    assert np.median(ea) <= 1e-7, np.median(ea)
+    assert np.abs(pot / rp - 1).max() <= 1e-6
+
+
+def test_fp64_acceleration_only_equals_full(nb, plummer1024):
+    """An FP64 context with jerk == NULL gives the same accelerations."""
+    cl = plummer1024
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nb.NB_FP64)
+    sim.predict(0)
+    act = torch.as_tensor(inputs.random_active(cl.n, 300, seed=2), device="cuda")
+    a1, _, p1 = sim.force(act)
+    a2, j2, p2 = sim.force(act, want_jerk=False)
+    torch.cuda.synchronize()
+    assert j2 is None and sim.status() == nb.NB_OK
+    assert torch.equal(a1, a2) and torch.equal(p1, p2)
+    sim.close()
