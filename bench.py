@@ -67,7 +67,8 @@ def parse():
                    help="run only nb_force on m random targets of N (profiling case)")
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--variant", type=int, default=None, help="mixed force kernel shape")
-    p.add_argument("--workload", default="step", choices=["step", "batch", "drift", "binaries"],
+    p.add_argument("--workload", default="step",
+                   choices=["step", "batch", "drift", "binaries", "leapfrog"],
                    help="step: the headline line; batch / drift / binaries: the other "
                         "configurations (their own JSON lines)")
     p.add_argument("--clusters", type=int, default=512)
@@ -187,6 +188,57 @@ def workload_drift(args):
     if base:
         out["mixed_over_fp64_drift"] = abs(comp) / abs(base)
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def workload_leapfrog(args):
+    """Acceleration-only workload: kick-drift-kick leapfrog with a shared step
+    (nb_step_leapfrog) on the N = 2^20 Kroupa Plummer sphere, mixed precision;
+    interactions/s over K timed steps, the force kernel at 20 flops per
+    interaction against the FP32 peak, and the relative energy change."""
+    import torch
+    from paper_1411_5234_gb300 import nbody
+    torch.cuda.set_device(0)
+    n, L = args.n, args.level
+    cl = make_cluster(n, 0)
+    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nbody.NB_MIXED, graph_steps=0)
+    dt_ticks = 1 << (sim.cfg.tick_exp - L)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sim.leapfrog(args.warmup, dt_ticks)
+    e0 = sum(sim.energy())
+    sim.profile(True)
+    sim.profile_read()
+    evs = []
+    with torch.cuda.stream(sim.stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(sim.stream)
+            sim.leapfrog(1, dt_ticks)
+            ev1.record(sim.stream)
+            evs.append((ev0, ev1))
+    sim.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    force_ms, launches = sim.profile_read()
+    e1 = sum(sim.energy())
+    assert sim.status() == nbody.NB_OK
+    rate = args.steps * n * n / (total_ms * 1e-3)
+    per = force_ms * 1e-3 / max(launches, 1)
+    achieved = FLOPS_PER_INTERACTION_ACC * n * n / per / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    print(json.dumps({
+        "workload": f"leapfrog (kick-drift-kick, shared step 2^-{L}): Plummer N={n} Kroupa, "
+                    "eps=1e-4, mixed, acceleration-only force",
+        "metric": "pair-interactions/s", "unit": UNIT, "value": rate, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_force_mixed (acceleration only)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "flops_per_interaction": FLOPS_PER_INTERACTION_ACC,
+                     "force_ms_per_launch": per * 1e3},
+        "energy_rel_change": (e1 - e0) / abs(e0),
+        "l2": "flushed between timed steps (256 MiB write)"}), flush=True)
+    sim.close()
     return 0
 
 
@@ -409,6 +461,8 @@ def main():
         return workload_batch(args)
     if args.workload in ("drift", "binaries"):
         return workload_drift(args)
+    if args.workload == "leapfrog":
+        return workload_leapfrog(args)
 
     import torch
     from paper_1411_5234_gb300 import inputs, nbody
@@ -591,9 +645,41 @@ def sweep(nbody, inputs, torch, cl):
             "flops_per_interaction": FLOPS_PER_INTERACTION_ACC,
             "frac_fp32_peak": (FLOPS_PER_INTERACTION_ACC * rate
                                / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6))})
+    # the mixed path's separation-mode bounds (NB_DS, NB_FP32) at m = 2^14
+    idx = inputs.random_active(n, 4096, seed=123)
+    act = torch.as_tensor(idx, device="cuda")
+    ref = sims["fp64"].force(act)
+    sims["fp64"].synchronize()
+    ra, rj = ref[0].cpu().numpy(), ref[1].cpu().numpy()
+    rel = lambda x, r: np.linalg.norm(x - r, axis=1) / np.linalg.norm(r, axis=1)
+    out["separation_modes"] = {}
+    for name, prec in (("ds", nbody.NB_DS), ("fp32", nbody.NB_FP32)):
+        s = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=prec, graph_steps=0)
+        s.predict(0)
+        s.profile(True)
+        m = n >> 6
+        a14 = torch.as_tensor(inputs.random_active(n, m, seed=6), device="cuda")
+        acc = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+        jerk = torch.empty_like(acc)
+        s.force(a14, acc, jerk, None, want_pot=False)
+        s.synchronize()
+        s.profile_read()
+        best = math.inf
+        for _ in range(3):
+            s.force(a14, acc, jerk, None, want_pot=False)
+            ms, cnt = s.profile_read()
+            best = min(best, ms / max(cnt, 1))
+        a, j, _ = s.force(act)
+        s.synchronize()
+        ea = rel(a.cpu().numpy(), ra)
+        ej = rel(j.cpu().numpy(), rj)
+        out["separation_modes"][name] = {
+            "m": m, "interactions_per_s": m * n / (best * 1e-3), "ms": best,
+            "acc_rel_max": float(ea.max()), "acc_rel_median": float(np.median(ea)),
+            "jerk_rel_median": float(np.median(ej))}
+        s.close()
     # accuracy: mixed vs FP64 on 4096 targets (GPU against GPU; the oracle
     # checks both paths at this size in tests/test_gpu_full_size.py)
-    idx = inputs.random_active(n, 4096, seed=123)
     act = torch.as_tensor(idx, device="cuda")
     res = {}
     for name in ("mixed", "fp64"):

@@ -30,6 +30,15 @@
  *              square roots included, in SP); sums over sources accumulated
  *              with a compensated FP32 pair per tile and combined in FP64;
  *              predictor, corrector, time, state and energy stay FP64.
+ *   NB_DS    : as NB_MIXED with double-single separations for every source
+ *              (no far-cell shortcut): the accuracy bound of the mixed path,
+ *              at a lower speed.
+ *   NB_FP32  : as NB_MIXED with plain FP32 separations for every source
+ *              (the offsets' low words unused): the speed bound, whose
+ *              separation error is relative to the cell size rather than to
+ *              the separation, so close pairs lose accuracy.
+ *   NB_DS and NB_FP32 use the 64 x 4 kernel shape (variant 2); nb_force
+ *   without jerk uses the mixed separations in every non-FP64 mode.
  *
  * Memory ownership
  *   All device memory is the caller's: nb_workspace_size() gives the bytes of
@@ -74,7 +83,7 @@ extern "C" {
 
 typedef struct nb_ctx nb_ctx;
 
-typedef enum { NB_FP64 = 0, NB_MIXED = 1 } nb_precision;
+typedef enum { NB_FP64 = 0, NB_MIXED = 1, NB_DS = 2, NB_FP32 = 3 } nb_precision;
 
 typedef struct {
     double  G;          /* gravitational constant (Eq. 1)                      */
@@ -164,6 +173,19 @@ int nb_step_block(nb_ctx *ctx, int64_t n_steps);
  * 2^-level_min time units keeps every particle synchronised there).
  * Default: no end time. */
 int nb_set_end_time(nb_ctx *ctx, int64_t t_end_ticks);
+
+/* Kick-drift-kick leapfrog with one shared step of dt_ticks ticks (> 0,
+ * at most 2^52), n_steps times, on every particle: v += a dt/2; x += v dt;
+ * a = the acceleration at the new positions (Eq. 1, Eq. 2; in a mixed
+ * context the acceleration-only kernel of nb_force without jerk); v += a dt/2;
+ * each particle's time advances by dt.  The acceleration-only workload of
+ * the same force sum, next to the Hermite block steps.  It starts from the
+ * stored acceleration, takes the sources at their stored positions (so every
+ * particle of a cluster should share one time, as after nb_init or an
+ * nb_set_state with equal times), leaves the stored jerk and potential as
+ * they were, and is not meant to be interleaved with nb_step_block.
+ * Asynchronous. */
+int nb_step_leapfrog(nb_ctx *ctx, int64_t n_steps, int64_t dt_ticks);
 
 /* FP64 kinetic and softened potential energy of cluster `cluster` (-1: all
  * clusters summed), with every particle predicted to its cluster's current

@@ -73,6 +73,12 @@ def _load():
         lib.oracle_init.argtypes = [i64, P, P, P, P, P, P, P, f64, f64, f64,
                                     i32, i32, i32]
         lib.oracle_init.restype = i32
+        lib.oracle_kick.argtypes = [i64, P, P, f64]
+        lib.oracle_kick.restype = None
+        lib.oracle_drift.argtypes = [i64, P, P, f64]
+        lib.oracle_drift.restype = None
+        lib.oracle_leapfrog.argtypes = [i64, P, P, P, P, f64, f64, f64, i64]
+        lib.oracle_leapfrog.restype = i32
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = i32
         lib.oracle_set_threads.argtypes = [i32]
@@ -192,6 +198,40 @@ def level(dt_crit, level_old, t_new_ticks, tick_exp, lmin, lmax):
     return int(_load().oracle_level(float(dt_crit), int(level_old),
                                     int(t_new_ticks), int(tick_exp), int(lmin),
                                     int(lmax)))
+
+
+def kick(vel, acc, h):
+    """Leapfrog half kick: returns ``vel + h * acc`` (copies)."""
+    vel = _f64(vel).reshape(-1, 3).copy()
+    n = vel.shape[0]
+    acc = _f64(acc, (n, 3))
+    _load().oracle_kick(n, _ptr(vel), _ptr(acc), float(h))
+    return vel
+
+
+def drift(pos, vel, dt):
+    """Leapfrog drift: returns ``pos + dt * vel`` (copies)."""
+    pos = _f64(pos).reshape(-1, 3).copy()
+    n = pos.shape[0]
+    vel = _f64(vel, (n, 3))
+    _load().oracle_drift(n, _ptr(pos), _ptr(vel), float(dt))
+    return pos
+
+
+def leapfrog(pos, vel, acc, mass, eps, dt, n_steps, G=1.0):
+    """Kick-drift-kick leapfrog with a shared step ``dt`` for ``n_steps``
+    steps, from positions, velocities and the acceleration at the start.
+    Returns ``(pos, vel, acc)`` at the end (copies)."""
+    pos = _f64(pos).reshape(-1, 3).copy()
+    n = pos.shape[0]
+    vel = _f64(vel, (n, 3)).copy()
+    acc = _f64(acc, (n, 3)).copy()
+    mass = _f64(mass, (n,))
+    rc = _load().oracle_leapfrog(n, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(mass),
+                                 float(G), float(eps), float(dt), int(n_steps))
+    if rc != 0:
+        raise MemoryError("oracle_leapfrog")
+    return pos, vel, acc
 
 
 class State:

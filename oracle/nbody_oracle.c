@@ -437,3 +437,43 @@ int oracle_init(int64_t n, const double *pos, const double *vel,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Kick-drift-kick leapfrog with one shared step: the acceleration-only */
+/* workload the same force sum (Eq. 1, Eq. 2) drives.  The paper's      */
+/* method needs the jerk for its Hermite scheme; this second-order,     */
+/* time-symmetric integrator needs the acceleration alone.  Per step:   */
+/*   kick  v <- v + a dt/2,  drift  x <- x + v dt,  a <- a(x),          */
+/*   kick  v <- v + a dt/2.                                             */
+/* oracle_kick and oracle_drift are the two halves on n x 3 arrays;     */
+/* oracle_leapfrog takes n_steps steps, acc holding a(x) at the start   */
+/* on entry and at the end on return.  Returns 0, or -1 when memory     */
+/* runs out.                                                            */
+/* ------------------------------------------------------------------ */
+void oracle_kick(int64_t n, double *vel, const double *acc, double h)
+{
+    for (int64_t i = 0; i < 3 * n; i++) vel[i] = vel[i] + h * acc[i];
+}
+
+void oracle_drift(int64_t n, double *pos, const double *vel, double dt)
+{
+    for (int64_t i = 0; i < 3 * n; i++) pos[i] = pos[i] + dt * vel[i];
+}
+
+int oracle_leapfrog(int64_t n, double *pos, double *vel, double *acc,
+                    const double *mass, double G, double eps, double dt,
+                    int64_t n_steps)
+{
+    int64_t *idx = malloc(sizeof *idx * (size_t)(n > 0 ? n : 1));
+    if (!idx) return -1;
+    for (int64_t i = 0; i < n; i++) idx[i] = i;
+    const double h = 0.5 * dt;
+    for (int64_t s = 0; s < n_steps; s++) {
+        oracle_kick(n, vel, acc, h);
+        oracle_drift(n, pos, vel, dt);
+        oracle_force(n, pos, vel, mass, G, eps, n, idx, acc, NULL, NULL);
+        oracle_kick(n, vel, acc, h);
+    }
+    free(idx);
+    return 0;
+}

@@ -86,7 +86,7 @@ bool config_ok(const nb_config* c) {
   if (!(c->eta_start > 0.0) || !std::isfinite(c->eta_start)) return false;
   if (c->tick_exp < 1 || c->tick_exp > kMaxTickExp) return false;
   if (c->level_min < 0 || c->level_min > c->level_max || c->level_max > c->tick_exp) return false;
-  if (c->precision != NB_FP64 && c->precision != NB_MIXED) return false;
+  if (c->precision < NB_FP64 || c->precision > NB_FP32) return false;
   if (c->bfactor < 0 || c->graph_steps < 0) return false;
   if (c->sort_sources != 0 && c->sort_sources != 1) return false;
   if (c->variant < 0 || c->variant >= force_mixed_variants()) return false;
@@ -206,7 +206,12 @@ namespace {
     if (e_ != cudaSuccess) return NB_ECUDA;    \
   } while (0)
 
-bool is_mixed(const nb_ctx* c) { return c->cfg.precision == NB_MIXED; }
+// every mode but FP64 uses the mixed source layout and kernel family
+bool is_mixed(const nb_ctx* c) { return c->cfg.precision != NB_FP64; }
+// separation mode of the mixed kernel (0: mixed vote, 1: DS, 2: plain FP32)
+int sep_mode(const nb_ctx* c) {
+  return c->cfg.precision == NB_DS ? 1 : c->cfg.precision == NB_FP32 ? 2 : 0;
+}
 
 ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, double* acc, int sa,
                      double* jerk, int sj, double* pot, int sp, bool f64_sources) {
@@ -326,6 +331,8 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
     e = launch_force_fp64(fa, c->grid_f64, pot_only ? kF64PotOnly : kF64Full, c->st);
   else if (acc_only)
     e = launch_force_mixed_acc(fa, c->grid_acc, pot != nullptr, c->st);
+  else if (sep_mode(c))
+    e = launch_force_mixed_sep(fa, c->grid_mix, pot != nullptr, sep_mode(c), c->st);
   else
     e = launch_force_mixed(fa, c->grid_mix, pot != nullptr, c->cfg.variant, c->st);
   if (e != cudaSuccess) return e;
@@ -442,6 +449,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
 
   nb_ctx* c = new nb_ctx();
   c->cfg = *cfg;
+  if (c->cfg.precision == NB_DS || c->cfg.precision == NB_FP32) c->cfg.variant = 2;
   c->st = static_cast<cudaStream_t>(stream);
   c->off_host.assign(offsets, offsets + n_clusters + 1);
   c->mass_host.assign(mass, mass + N);
@@ -496,7 +504,8 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
     delete c;
     return NB_ECUDA;
   }
-  c->grid_mix = sms * force_mixed_ctas_per_sm(cfg->variant);
+  c->grid_mix = sep_mode(c) ? sms * force_mixed_sep_ctas_per_sm(sep_mode(c))
+                            : sms * force_mixed_ctas_per_sm(c->cfg.variant);
   c->grid_f64 = sms * force_fp64_ctas_per_sm();
   c->grid_acc = sms * force_mixed_acc_ctas_per_sm();
   c->sms = sms;
@@ -555,9 +564,10 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
     const bool f64 = !is_mixed(c);
     double* an = reinterpret_cast<double*>(d.acc_new);
     double* jn = reinterpret_cast<double*>(d.jerk_new);
+    // every particle, targets in slot order, results to their particle rows
     if (launch_predict(d, nullptr, 0, cfg->tick_exp, !f64, f64, false, st) ||
-        launch_actoff_identity(d, st) ||
-        enqueue_force(c, nullptr, nullptr, an, 4, jn, 4, an + 3, 4, f64, 0, 0, false, N) ||
+        launch_slot_list(d, st) || launch_actoff_identity(d, st) ||
+        enqueue_force(c, d.active, d.active, an, 4, jn, 4, an + 3, 4, f64, 0, 0, false, N) ||
         launch_init_levels(d, cfg->eta_start, cfg->tick_exp, cfg->level_min, cfg->level_max, st)) {
       rc = NB_ECUDA;
       break;
@@ -625,6 +635,28 @@ int nb_correct(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
   ca.lmin = c->cfg.level_min;
   ca.lmax = c->cfg.level_max;
   NB_TRY(launch_correct(c->d, ca, m, c->st));
+  return NB_OK;
+}
+
+int nb_step_leapfrog(nb_ctx* c, int64_t n_steps, int64_t dt_ticks) {
+  if (!c || n_steps < 0 || dt_ticks <= 0 || dt_ticks > ((int64_t)1 << 52)) return NB_EINVAL;
+  if (n_steps == 0) return NB_OK;
+  const bool f64 = !is_mixed(c);
+  const int T = c->cfg.tick_exp;
+  const double dt = std::ldexp(static_cast<double>(dt_ticks), -T);
+  double* an = reinterpret_cast<double*>(c->d.acc_new);
+  for (int64_t s = 0; s < n_steps; ++s) {
+    NB_TRY(launch_leapfrog(c->d, nullptr, 0.5 * dt, dt, dt_ticks, c->st));  // kick, drift
+    NB_TRY(launch_predict(c->d, nullptr, 0, T, !f64, f64, false, c->st, true));
+    NB_TRY(launch_slot_list(c->d, c->st));
+    NB_TRY(launch_actoff_identity(c->d, c->st));
+    // acceleration at the new positions: no jerk (the acceleration-only
+    // kernel), targets in slot order, results to their particle rows
+    NB_TRY(enqueue_force(c, c->d.active, c->d.active, an, 4, nullptr, 0, nullptr, 0, f64, 0, 1,
+                         false, c->d.N));
+    NB_TRY(launch_leapfrog(c->d, an, 0.5 * dt, dt, 0, c->st));  // kick
+  }
+  NB_TRY(launch_tcur_from_t(c->d, c->st));
   return NB_OK;
 }
 
@@ -816,7 +848,7 @@ int nb_tile_stats(nb_ctx* c, int64_t* warp_tiles, int64_t* near_warp_tiles) {
 
 int nb_autotune(nb_ctx* c, int32_t* variant_out, double* ms_out) {
   if (!c) return NB_EINVAL;
-  if (c->cfg.precision != NB_MIXED) {  // one FP64 shape: nothing to choose
+  if (c->cfg.precision != NB_MIXED) {  // FP64, DS, FP32: one shape each, nothing to choose
     if (variant_out) *variant_out = c->cfg.variant;
     return NB_OK;
   }

@@ -25,6 +25,10 @@ template <bool POT> using S5 = mixk::MixShape<32, 4, POT, false, true, 1, 8>;
 // of the 64x4 (5 or 6 CTAs/SM, unrolled or not), 128x2 and 256x1 shapes at
 // N = m = 2^20 (measured on GB300)
 template <bool POT> using SA = mixk::MixShape<64, 4, POT, false, true, 1, 6, false>;
+// the 64 x 4 shape with double-single separations everywhere, and with plain
+// FP32 separations (NB_DS, NB_FP32: accuracy and speed bounds of the mixed path)
+template <bool POT> using SD = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepDS>;
+template <bool POT> using SF = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepFP32>;
 
 template <class Sh>
 cudaError_t launch_shape(const ForceArgs& a, int grid, cudaStream_t st) {
@@ -84,6 +88,15 @@ int force_mixed_ctas_per_sm(int variant) {
 }
 
 int force_mixed_acc_ni() { return SA<false>::NI; }
+int force_mixed_sep_ctas_per_sm(int sep) {
+  return sep == mixk::kSepDS ? occupancy_both<SD>() : occupancy_both<SF>();
+}
+cudaError_t launch_force_mixed_sep(const ForceArgs& a, int grid, bool with_pot, int sep,
+                                   cudaStream_t st) {
+  if (sep == mixk::kSepDS)
+    return with_pot ? launch_shape<SD<true>>(a, grid, st) : launch_shape<SD<false>>(a, grid, st);
+  return with_pot ? launch_shape<SF<true>>(a, grid, st) : launch_shape<SF<false>>(a, grid, st);
+}
 int force_mixed_acc_ctas_per_sm() { return occupancy_both<SA>(); }
 cudaError_t launch_force_mixed_acc(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st) {
   return with_pot ? launch_shape<SA<true>>(a, grid, st) : launch_shape<SA<false>>(a, grid, st);

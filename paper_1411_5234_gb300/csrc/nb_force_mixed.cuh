@@ -69,11 +69,17 @@ constexpr float kFarRatio2 = 4.0f;
 // component order inside a group of 4 sources (float4 index)
 enum { cDXH = 0, cDYH, cDZH, cM, cVX, cVY, cVZ, cDXL, cDYL, cDZL };
 
+// separation modes: the far/near vote of the mixed path; double-single
+// separations for every cell; plain FP32 separations (no low words) for every
+// cell, the targets' own cell still through the masked single-target loop
+enum { kSepMixed = 0, kSepDS = 1, kSepFP32 = 2 };
+
 template <int NT_, int IPT_, bool POT_, bool RCP_, bool SMT_, int UNR_, int MINB_,
-          bool JERK_ = true>
+          bool JERK_ = true, int SEP_ = kSepMixed>
 struct MixShape {
   static constexpr int NT = NT_, IPT = IPT_, NI = NT_ * IPT_, UNR = UNR_, MINB = MINB_;
   static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_, JERK = JERK_;
+  static constexpr int SEP = SEP_;
   static_assert(NT_ * IPT_ <= kMixNI, "partial-sum rows hold at most kMixNI targets");
 };
 
@@ -180,7 +186,8 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ tile, int ng
 
 // Near cell, one target: d = (dh_j + eh) + (dl_j + el).  Near cells are a
 // small fraction, so each target takes its own pass over the cell and only
-// one target's low parts are live at a time.
+// one target's low parts are live at a time.  (Plain FP32 separation mode:
+// d = dh_j + eh, the low words unused.)
 template <class Sh, bool MASK>
 __device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile, int ngroups,
                                               int64_t slot0, Target& s, f2 elx, f2 ely, f2 elz,
@@ -191,6 +198,16 @@ __device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile, i
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
                      vy = G[cVY], vz = G[cVZ], dxl = G[cDXL], dyl = G[cDYL], dzl = G[cDZL];
     const int64_t js = slot0 + 4 * g;
+    if constexpr (Sh::SEP == kSepFP32) {
+      pair_tail<Sh, MASK>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
+                          f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
+                          eps2, js, slot);
+      pair_tail<Sh, MASK>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
+                          f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
+                          eps2, js + 2, slot);
+      (void)dxl; (void)dyl; (void)dzl; (void)elx; (void)ely; (void)elz;
+      continue;
+    }
     pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.x, s.ex), f2_add(dxl.x, elx)),
                         f2_add(f2_add(dyh.x, s.ey), f2_add(dyl.x, ely)),
                         f2_add(f2_add(dzh.x, s.ez), f2_add(dzl.x, elz)), f2_add(vx.x, s.nvx),
@@ -438,7 +455,21 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
         }
         const float4* cell = stage[st] + g0 * kGroupF4;
         const int64_t c0 = t0 + 4 * g0;
-        if (__all_sync(0xffffffffu, far)) {
+        bool take_far;
+        if constexpr (Sh::SEP == kSepMixed) {
+          take_far = __all_sync(0xffffffffu, far);
+        } else if constexpr (Sh::SEP == kSepDS) {
+          take_far = false;
+        } else {  // FP32: far arithmetic unless the cell holds a target of the warp
+          bool own = false;
+#pragma unroll
+          for (int r = 0; r < IPT; ++r) {
+            const long long sl = tpos.slot[r][tid];
+            own = own || (sl >= c0 && sl < c0 + 4 * ngq);
+          }
+          take_far = !__any_sync(0xffffffffu, own);
+        }
+        if (take_far) {
           if (ngq == kCellGroups)
             tile_far<Sh, kCellGroups>(cell, ngq, tg, eps2);
           else

@@ -146,7 +146,8 @@ __global__ void k_scan(Dev d, int32_t nblk) {
 // the tile's particles due at the target time.
 __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* t_tgt,
                                                           int64_t t_fixed, int T, int write_mix,
-                                                          int write64, int count_due) {
+                                                          int write64, int count_due,
+                                                          int zero_tau) {
   __shared__ float shd[kMixJT / 32];
   __shared__ int32_t shi[32];
   const int32_t tile = blockIdx.x;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
   if (p >= 0) {
     const int64_t ti = d.t[p];
     due = (count_due && ti + step_ticks(d.level[p], T) == tn) ? 1 : 0;
-    const double tau = ldexp((double)(tn - ti), -T);
+    const double tau = zero_tau ? 0.0 : ldexp((double)(tn - ti), -T);
     const dbl4 P = d.pos[p], V = d.vel[p], A = d.acc[p], J = d.jerk[p];
     predict1(P, V, A, J, tau, xp, vp);
     m = P.w;
@@ -719,6 +720,55 @@ __global__ void k_unpack3(const dbl4* src, double* dst3, int64_t n) {
 }
 
 // Current block time of each cluster = the latest particle time in it.
+// Kick-drift-kick leapfrog halves on every particle (nb_step_leapfrog).
+// a_new == nullptr: kick with the stored acceleration and drift,
+//   v <- v + h a, x <- x + dt v, t <- t + dt_ticks;
+// otherwise: kick with the new acceleration (rows of 4 doubles) and store it,
+//   v <- v + h a_new, a <- a_new (the potential word is kept).
+__global__ void k_leapfrog(Dev d, const double* a_new, double h, double dt, int64_t dt_ticks) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    dbl4 v = d.vel[i];
+    if (a_new == nullptr) {
+      const dbl4 a = d.acc[i];
+      v.x = v.x + h * a.x;
+      v.y = v.y + h * a.y;
+      v.z = v.z + h * a.z;
+      dbl4 p = d.pos[i];
+      p.x = p.x + dt * v.x;
+      p.y = p.y + dt * v.y;
+      p.z = p.z + dt * v.z;
+      d.pos[i] = p;
+      d.t[i] += dt_ticks;
+    } else {
+      const double ax = a_new[4 * i], ay = a_new[4 * i + 1], az = a_new[4 * i + 2];
+      v.x = v.x + h * ax;
+      v.y = v.y + h * ay;
+      v.z = v.z + h * az;
+      dbl4 a = d.acc[i];
+      a.x = ax;
+      a.y = ay;
+      a.z = az;
+      d.acc[i] = a;
+    }
+    d.vel[i] = v;
+  }
+}
+
+// Every particle as a target list in source-slot order (the spatial order
+// of the tiles, so the warps of the force kernel get compact target groups):
+// active[off[k] + r] = sperm[soff[k] + r] for the N_k leading slots of each
+// cluster (its pad slots come last).
+__global__ void k_slot_list(Dev d) {
+  const int64_t S = d.soff[d.K];
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = upper_bound_i64(d.soff, d.K + 1, s) - 1;
+    const int64_t r = s - d.soff[k];
+    if (r < d.off[k + 1] - d.off[k]) d.active[d.off[k] + r] = d.sperm[s];
+  }
+}
+
 __global__ void k_tcur_from_t(Dev d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -742,9 +792,18 @@ cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T,
-                           bool mix, bool f64, bool count_due, cudaStream_t st) {
+                           bool mix, bool f64, bool count_due, cudaStream_t st, bool zero_tau) {
   k_predict_tiles<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d, t_tgt, t_fixed, T, mix,
-                                                                  f64, count_due);
+                                                                  f64, count_due, zero_tau);
+  return cudaGetLastError();
+}
+cudaError_t launch_slot_list(const Dev& d, cudaStream_t st) {
+  k_slot_list<<<blocks_for(d.N + 4 * d.K, 256), 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_leapfrog(const Dev& d, const double* a_new, double h, double dt,
+                            int64_t dt_ticks, cudaStream_t st) {
+  k_leapfrog<<<blocks_for(d.N, 256), 256, 0, st>>>(d, a_new, h, dt, dt_ticks);
   return cudaGetLastError();
 }
 cudaError_t launch_scan_plan_scatter(const Dev& d, const PlanArgs& p, int T, cudaStream_t st) {

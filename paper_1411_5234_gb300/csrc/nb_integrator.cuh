@@ -128,8 +128,14 @@ struct CorrectArgs {
 
 cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t st);
 cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st);
+// zero_tau: sources at the stored positions (no Taylor step)
 cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T, bool mix,
-                           bool f64, bool count_due, cudaStream_t st);
+                           bool f64, bool count_due, cudaStream_t st, bool zero_tau = false);
+// every particle in source-slot order into d.active (use it as the rows too)
+cudaError_t launch_slot_list(const Dev& d, cudaStream_t st);
+// leapfrog halves (a_new == nullptr: kick + drift + time; else kick + store)
+cudaError_t launch_leapfrog(const Dev& d, const double* a_new, double h, double dt,
+                            int64_t dt_ticks, cudaStream_t st);
 // block step: scan + plan (one CTA), then the active list
 cudaError_t launch_scan_plan_scatter(const Dev& d, const PlanArgs& p, int T, cudaStream_t st);
 cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st);

@@ -252,6 +252,16 @@ __device__ __forceinline__ int32_t upper_bound_i32(const int32_t* a, int32_t n, 
   return lo;
 }
 
+__device__ __forceinline__ int32_t upper_bound_i64(const int64_t* a, int32_t n, int64_t v) {
+  // first index k in [0, n) with a[k] > v (a ascending)
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) > v) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
 __host__ __device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t round_up64(int64_t a, int64_t b) { return ceil_div64(a, b) * b; }
 
@@ -274,6 +284,11 @@ int force_mixed_ctas_per_sm(int variant);
 cudaError_t launch_force_mixed_acc(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st);
 int force_mixed_acc_ni();
 int force_mixed_acc_ctas_per_sm();
+// the 64 x 4 shape (force_mixed_ni(2) targets per item) with another
+// separation mode: 1 double-single everywhere, 2 plain FP32
+cudaError_t launch_force_mixed_sep(const ForceArgs& a, int grid, bool with_pot, int sep,
+                                   cudaStream_t st);
+int force_mixed_sep_ctas_per_sm(int sep);
 int force_fp64_ctas_per_sm();
 size_t force_mixed_smem();
 size_t force_fp64_smem();

@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ETIMEOUT, NB_ENONFINITE, NB_ESTATE = range(7)
-NB_FP64, NB_MIXED = 0, 1
+NB_FP64, NB_MIXED, NB_DS, NB_FP32 = 0, 1, 2, 3
 MIXED_VARIANTS = 6    # NB_MIXED_VARIANTS: shapes of the mixed force kernel
 
 FUNCTIONS = [
@@ -25,7 +25,7 @@ FUNCTIONS = [
     "nb_correct", "nb_step_block", "nb_set_end_time", "nb_energy", "nb_get_state",
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
     "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
-    "nb_energies", "nb_autotune",
+    "nb_energies", "nb_autotune", "nb_step_leapfrog",
 ]
 
 
@@ -64,6 +64,7 @@ def _load() -> ctypes.CDLL:
         "nb_force": (ctypes.c_int, [P, P, i64, P, P, P]),
         "nb_correct": (ctypes.c_int, [P, i64, P, i64, P, P]),
         "nb_step_block": (ctypes.c_int, [P, i64]),
+        "nb_step_leapfrog": (ctypes.c_int, [P, i64, i64]),
         "nb_set_end_time": (ctypes.c_int, [P, i64]),
         "nb_energy": (ctypes.c_int, [P, i32, P, P]),
         "nb_get_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
@@ -225,6 +226,10 @@ class Sim:
 
     def step(self, n_steps: int = 1):
         _check(lib.nb_step_block(self._ctx, int(n_steps)), "nb_step_block")
+
+    def leapfrog(self, n_steps: int, dt_ticks: int):
+        """Kick-drift-kick leapfrog, shared step of ``dt_ticks`` ticks."""
+        _check(lib.nb_step_leapfrog(self._ctx, int(n_steps), int(dt_ticks)), "nb_step_leapfrog")
 
     def set_end_time(self, t_end_ticks: int):
         _check(lib.nb_set_end_time(self._ctx, int(t_end_ticks)), "nb_set_end_time")

@@ -249,3 +249,36 @@ def test_full_size_acceleration_only_sampled(nb, cluster):
     ea = rel_err(acc, ra)
     assert np.median(ea) <= 1e-7 and np.quantile(ea, 0.999) <= 1e-6
     assert np.abs(pot / rp - 1).max() <= 1e-6
+
+
+def test_full_size_leapfrog_step_sampled(nb, cluster):
+    """One mixed leapfrog step at N = 2^20 from seeded synthetic a0: the
+    oracle kicks and drifts every particle, then evaluates the force and the
+    second kick of sampled particles one by one."""
+    cl = cluster
+    L = 10
+    dt, h = 2.0 ** -L, 2.0 ** -(L + 1)
+    a0 = inputs.random_vectors(N, 2.0, seed=41)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=EPS, precision=nb.NB_MIXED)
+    try:
+        sim.set_state(cl.pos, cl.vel, a0, np.zeros((N, 3)), np.zeros(N, dtype=np.int64),
+                      np.full(N, L, dtype=np.int32))
+        sim.leapfrog(1, 1 << (sim.cfg.tick_exp - L))
+        s = sim.get_state()
+        assert sim.status() == nb.NB_OK
+    finally:
+        sim.close()
+    vh = oracle.kick(cl.vel, a0, h)
+    x1 = oracle.drift(cl.pos, vh, dt)
+    sample = inputs.random_active(N, 128, seed=42).astype(np.int64)
+    a1, _, _ = oracle.force(x1, vh, cl.mass, EPS, idx=sample)
+    v1 = oracle.kick(vh[sample], a1, h)
+    nrm = lambda v: np.linalg.norm(v, axis=1)
+    Sa, _ = term_sums_big(x1, vh, cl.mass, EPS, sample)
+    assert (nrm(s["acc"][sample] - a1) / Sa).max() <= 1e-6
+    assert np.all(nrm(s["pos"][sample] - x1[sample])
+                  <= 4e-16 * (nrm(cl.pos[sample]) + dt * nrm(vh[sample])))
+    assert np.all(nrm(s["vel"][sample] - v1)
+                  <= 1.01 * h * nrm(s["acc"][sample] - a1)
+                  + 4e-16 * (nrm(cl.vel[sample]) + h * (nrm(a0[sample]) + nrm(a1))))
+    assert np.all(s["t"] == 1 << (40 - L))

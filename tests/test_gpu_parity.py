@@ -440,3 +440,104 @@ def test_fp64_acceleration_only_equals_full(nb, plummer1024):
     assert j2 is None and sim.status() == nb.NB_OK
     assert torch.equal(a1, a2) and torch.equal(p1, p2)
     sim.close()
+
+
+# ----------------------------------- separation modes (DS, plain FP32) ----
+
+def test_ds_mode_parity(nb):
+    """NB_DS (double-single separations for every source) meets the mixed
+    gates, close binary included."""
+    n = 4099
+    cl = inputs.plummer(n, seed=7, imf="kroupa")
+    idx = np.arange(n)
+    a, j, p = gpu_force(nb, cl, 1e-4, idx, nb.NB_DS)
+    ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx)
+    check_mixed(a, j, ra, rj, *term_sums(cl, 1e-4, idx))
+    assert np.abs(p / rp - 1).max() <= 1e-6
+    c2 = inputs.plummer(256, seed=2)
+    pos = c2.pos.copy()
+    pos[1] = pos[0] + np.array([1e-6, 0.0, 0.0])
+    c3 = inputs.Cluster(pos, c2.vel, c2.mass, c2.offsets)
+    a, _, _ = gpu_force(nb, c3, 0.0, [0, 1], nb.NB_DS)
+    ra, _, _ = oracle.force(pos, c2.vel, c2.mass, 0.0, idx=[0, 1])
+    assert rel_err(a, ra).max() <= 1e-5
+
+
+def test_fp32_mode_bounds(nb):
+    """NB_FP32 (plain FP32 separations): on a Plummer sample its error stays
+    within FP32 rounding relative to the cell size (condition-scaled 1e-4
+    here); a hard binary is not resolved (the pair force is off by orders of
+    magnitude more than in the mixed path), which is what the double-single
+    separations of the mixed path are for."""
+    n = 4099
+    cl = inputs.plummer(n, seed=7, imf="kroupa")
+    idx = np.arange(n)
+    a, j, p = gpu_force(nb, cl, 1e-4, idx, nb.NB_FP32)
+    ra, rj, rp = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4, idx=idx)
+    Sa, Sj = term_sums(cl, 1e-4, idx)
+    assert (np.linalg.norm(a - ra, axis=1) / Sa).max() <= 1e-4
+    assert np.all(np.isfinite(j)) and np.abs(p / rp - 1).max() <= 1e-4
+    c2 = inputs.plummer(256, seed=2)
+    pos = c2.pos.copy()
+    pos[1] = pos[0] + np.array([1e-6, 0.0, 0.0])
+    c3 = inputs.Cluster(pos, c2.vel, c2.mass, c2.offsets)
+    af, _, _ = gpu_force(nb, c3, 0.0, [0, 1], nb.NB_FP32)
+    am, _, _ = gpu_force(nb, c3, 0.0, [0, 1], nb.NB_MIXED)
+    ra, _, _ = oracle.force(pos, c2.vel, c2.mass, 0.0, idx=[0, 1])
+    assert rel_err(af, ra).max() > 100 * rel_err(am, ra).max()
+    assert rel_err(af, ra).max() > 1e-3
+
+
+# --------------------------------------------------------- leapfrog ----
+
+def _leapfrog_gpu(nb, cl, eps, a0, prec, n_steps, dt_level, flip=False):
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=eps, precision=prec)
+    try:
+        sim.set_state(cl.pos, -cl.vel if flip else cl.vel, a0, np.zeros((cl.n, 3)),
+                      np.zeros(cl.n, dtype=np.int64), np.full(cl.n, 10, dtype=np.int32))
+        sim.leapfrog(n_steps, 1 << (sim.cfg.tick_exp - dt_level))
+        s = sim.get_state()
+        assert sim.status() == nb.NB_OK
+        return s
+    finally:
+        sim.close()
+
+
+def test_leapfrog_fp64_matches_oracle(nb, plummer1024):
+    cl = plummer1024
+    a0 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4)[0]
+    s = _leapfrog_gpu(nb, cl, 1e-4, a0, nb.NB_FP64, 16, 10)
+    x, v, a = oracle.leapfrog(cl.pos, cl.vel, a0, cl.mass, 1e-4, 2.0 ** -10, 16)
+    assert np.abs(s["pos"] - x).max() <= 1e-12 * np.abs(x).max()
+    assert np.abs(s["vel"] - v).max() <= 1e-12 * np.abs(v).max()
+    assert rel_err(s["acc"], a).max() <= 1e-12
+    assert np.all(s["t"] == 16 << (40 - 10))
+
+
+def test_leapfrog_fp64_time_reversible(nb):
+    cl = inputs.plummer(512, seed=8)
+    a0 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)[0]
+    s = _leapfrog_gpu(nb, cl, 1e-2, a0, nb.NB_FP64, 32, 8)
+    back = inputs.Cluster(s["pos"], s["vel"], cl.mass, cl.offsets)
+    r = _leapfrog_gpu(nb, back, 1e-2, s["acc"], nb.NB_FP64, 32, 8, flip=True)
+    assert np.abs(r["pos"] - cl.pos).max() < 1e-11
+    assert np.abs(-r["vel"] - cl.vel).max() < 1e-11
+
+
+def test_leapfrog_mixed_matches_oracle(nb):
+    """Mixed leapfrog (acceleration-only kernel) against the oracle: the
+    kicks carry the force error, |dv| <= n dt 1e-6 sum_j |a_ij| and
+    |dx| <= n^2 dt^2 1e-6 sum_j |a_ij| over n steps (positions barely move,
+    so the term sums at the start bound every step's)."""
+    n, steps, L = 4099, 8, 10
+    cl = inputs.plummer(n, seed=9, imf="kroupa")
+    a0 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4)[0]
+    s = _leapfrog_gpu(nb, cl, 1e-4, a0, nb.NB_MIXED, steps, L)
+    x, v, a = oracle.leapfrog(cl.pos, cl.vel, a0, cl.mass, 1e-4, 2.0 ** -L, steps)
+    Sa, _ = term_sums(cl, 1e-4, np.arange(n))
+    dt = 2.0 ** -L
+    dv = np.linalg.norm(s["vel"] - v, axis=1)
+    dx = np.linalg.norm(s["pos"] - x, axis=1)
+    assert np.all(dv <= 2 * steps * dt * 1e-6 * Sa + 1e-14)
+    assert np.all(dx <= 2 * steps ** 2 * dt ** 2 * 1e-6 * Sa + 1e-14)
+    assert (np.linalg.norm(s["acc"] - a, axis=1) / Sa).max() <= 2e-6

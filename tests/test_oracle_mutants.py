@@ -39,6 +39,12 @@ MUTANTS = {
     "energy_pair_mass": ("nsum_add(&p, -G * mass[i] * mass[j] / s);", "nsum_add(&p, -G * mass[j] / s);"),
     "kinetic_factor": ("nsum_add(&k, 0.5 * mass[i] * v2);", "nsum_add(&k, mass[i] * v2);"),
     "angular_momentum_sign": ("(r[0] * v[1] - r[1] * v[0])", "(r[1] * v[0] - r[0] * v[1])"),
+    "leapfrog_full_kick": ("const double h = 0.5 * dt;", "const double h = dt;"),
+    "leapfrog_second_kick_dropped": ("""        oracle_force(n, pos, vel, mass, G, eps, n, idx, acc, NULL, NULL);
+        oracle_kick(n, vel, acc, h);""", """        oracle_force(n, pos, vel, mass, G, eps, n, idx, acc, NULL, NULL);"""),
+    "leapfrog_drift_before_kick": ("""        oracle_kick(n, vel, acc, h);
+        oracle_drift(n, pos, vel, dt);""", """        oracle_drift(n, pos, vel, dt);
+        oracle_kick(n, vel, acc, h);"""),
 }
 
 

@@ -397,3 +397,54 @@ def test_block_step_invariants_and_conservation():
     # P are conserved only to truncation level (scale: sum m |v| ~ 0.7)
     np.testing.assert_allclose(L1, L0, atol=1e-7)
     np.testing.assert_allclose(P1, P0, atol=1e-7)
+
+
+# ------------------------------------------------- leapfrog (KDK) ----
+
+def test_leapfrog_free_motion():
+    # G = 0: no force, so velocities stay exactly and positions move by
+    # n dt v (dt a power of two: every product exact, one rounding per add)
+    rng = np.random.default_rng(5)
+    pos, vel = rng.normal(size=(16, 3)), rng.normal(size=(16, 3))
+    x, v, a = oracle.leapfrog(pos, vel, np.zeros((16, 3)), np.ones(16), 0.1, 2.0 ** -6, 64, G=0.0)
+    assert np.array_equal(v, vel) and np.array_equal(a, np.zeros((16, 3)))
+    assert np.allclose(x, pos + 64 * 2.0 ** -6 * vel, rtol=0, atol=1e-13)
+
+
+def test_leapfrog_time_reversible():
+    # kick-drift-kick is time-symmetric: n steps, reversed velocities, n
+    # steps, reversed again returns the start to round-off
+    cl = inputs.plummer(32, seed=4)
+    a0 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)[0]
+    x, v, a = oracle.leapfrog(cl.pos, cl.vel, a0, cl.mass, 1e-2, 2.0 ** -8, 64)
+    x2, v2, _ = oracle.leapfrog(x, -v, a, cl.mass, 1e-2, 2.0 ** -8, 64)
+    assert np.abs(x2 - cl.pos).max() < 1e-11
+    assert np.abs(-v2 - cl.vel).max() < 1e-11
+    assert np.abs(x - cl.pos).max() > 1e-3      # it did move
+
+
+def test_leapfrog_second_order_kepler():
+    # closed-form Kepler orbit (e = 0.5, one period): the scheme is second
+    # order, so halving dt cuts the error by ~2^2
+    M = 4 * math.pi ** 2
+    m1, m2 = 0.6 * M, 0.4 * M
+    xk, vk = _kepler_state(1.0, 0.5, M, 0.0)
+    pos = np.array([-m2 / M * xk, m1 / M * xk])
+    vel = np.array([-m2 / M * vk, m1 / M * vk])
+    mass = np.array([m1, m2])
+    a0 = oracle.force(pos, vel, mass, 0.0)[0]
+    xr, _ = _kepler_state(1.0, 0.5, M, 1.0)
+    errs = []
+    for L in (10, 11, 12):
+        x, v, _ = oracle.leapfrog(pos, vel, a0, mass, 0.0, 2.0 ** -L, 2 ** L)
+        errs.append(np.linalg.norm((x[1] - x[0]) - xr))
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.5 < e1 / e2 < 4.5, errs
+
+
+def test_leapfrog_conserves_momentum():
+    cl = inputs.plummer(64, seed=6)
+    a0 = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)[0]
+    p0 = (cl.mass[:, None] * cl.vel).sum(0)
+    _, v, _ = oracle.leapfrog(cl.pos, cl.vel, a0, cl.mass, 1e-2, 2.0 ** -8, 32)
+    assert np.abs((cl.mass[:, None] * v).sum(0) - p0).max() < 1e-13
