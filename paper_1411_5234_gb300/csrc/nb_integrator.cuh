@@ -7,12 +7,12 @@
 namespace nb {
 
 // i-split factors up to kReduceSerial are reduced by one lane per target
-// (k_reduce); larger ones by k_reduce_wide in segments of kWideRows partial
+// (k_reduce); larger ones, in the same kernel, in segments of kWideRows partial
 // rows (one per warp of its CTA).
 constexpr int kReduceSerial = 16;
 constexpr int kWideRows = 32;
 
-// Entries of the k_reduce_wide arrival counters for a partial-sum buffer of
+// Entries of k_reduce's arrival counters (large splits) for a partial-sum buffer of
 // part_items work items.  The plan keeps sum_k T_k B_k <= part_items (T_k
 // i-tiles of cluster k), so the units (i-tile, row segment) of clusters with
 // B_k > kReduceSerial, sum_k T_k ceil(B_k / kWideRows), stay below

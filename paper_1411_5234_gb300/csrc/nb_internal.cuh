@@ -58,7 +58,7 @@ struct Dev {
   int32_t* active = nullptr;
   dbl4 *acc_new = nullptr, *jerk_new = nullptr;
   float4* src_mix = nullptr;     // (S / 4) * 10 float4
-  float4* tiles = nullptr;       // kTileRecF4 float4 per mixed source tile: per cell (c_hi, h), (c_lo, 0)
+  float4* tiles = nullptr;       // kTileRecF4 float4 per mixed source tile: per cell (c, h), (c_lo = 0, 0)
   int32_t* toff = nullptr;       // K + 1: first tile of each cluster
   int64_t n_tiles = 0;
   int32_t* sperm = nullptr;      // S: particle of each source slot (-1: pad)
@@ -73,8 +73,8 @@ struct Dev {
   int64_t *off = nullptr, *soff = nullptr;   // K + 1
   int64_t *t_cur = nullptr, *t_min = nullptr; // K
   int32_t *act_off = nullptr, *item_off = nullptr; // K + 1
-  int32_t* wt_off = nullptr;     // K + 1: (i-tile, row segment) units of k_reduce_wide
-  int32_t* wide_cnt = nullptr;   // k_reduce_wide arrival counters (zero between launches)
+  int32_t* wt_off = nullptr;     // K + 1: (i-tile, row segment) units of k_reduce's large splits
+  int32_t* wide_cnt = nullptr;   // their arrival counters (zero between launches)
   int32_t* bfac = nullptr;       // K
   double* esum = nullptr;        // energy partial sums
   uint32_t* status = nullptr;
