@@ -63,3 +63,12 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", "import paper_1411_5234_gb300.nbody"], cwd=ROOT,
                        env=env, capture_output=True, text=True)
     assert r.returncode != 0 and "not found" in r.stderr
+
+
+def test_precision_modes_in_config(libpath):
+    from paper_1411_5234_gb300 import nbody
+    for prec in (nbody.NB_FP64, nbody.NB_MIXED, nbody.NB_DS, nbody.NB_FP32):
+        cfg = nbody.default_config(precision=prec)
+        assert nbody.workspace_size(1000, 1, cfg) > 0
+    with pytest.raises(nbody.NBError):
+        nbody.workspace_size(1000, 1, nbody.default_config(precision=4))

@@ -58,3 +58,33 @@ def test_single_rank_helpers():
     import bench
     assert bench.reduce_max(42.0) == 42.0
     assert bench.job_rate(10, 4, 2.0) == 20.0
+
+
+def test_bench_traffic_follows_the_kernel_source(tmp_path):
+    """roofline.traffic is the committed ncu figure only while the kernel
+    source it was measured on is unchanged."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import re
+    sha = bench.kernel_source_sha(bench.KERNEL_FILES)
+    assert sha == bench.kernel_source_sha(bench.KERNEL_FILES)
+    text = open(os.path.join(ROOT, "profiles", "force_mixed_n1048576.md")).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha256:\s*([0-9a-f]+)", text)
+    assert m is not None and float(m.group(1)) > 0
+    got = bench.traffic_from_profile(bench.KERNEL_FILES)
+    assert got == (float(m.group(1)) if m.group(2) == sha else None)
+    other = tmp_path / "changed_kernel.cuh"
+    other.write_text("// a different kernel source\n")
+    assert bench.traffic_from_profile(bench.KERNEL_FILES + [str(other)]) is None
+
+
+def test_random_vectors_are_seeded_and_bounded():
+    sys.path.insert(0, ROOT)
+    from paper_1411_5234_gb300 import inputs
+    a = inputs.random_vectors(4000, 2.0, seed=3, lo=0.5)
+    b = inputs.random_vectors(4000, 2.0, seed=3, lo=0.5)
+    c = inputs.random_vectors(4000, 2.0, seed=4, lo=0.5)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    r = np.linalg.norm(a, axis=1)
+    assert r.min() >= 0.5 and r.max() < 2.0
+    assert np.abs(a.mean(0)).max() < 0.1          # isotropic directions
