@@ -6,6 +6,7 @@ extended-precision brute force, chosen so that a dropped term, a wrong sign or
 exponent, or a transposed operand in the oracle fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -448,3 +449,22 @@ def test_leapfrog_conserves_momentum():
     p0 = (cl.mass[:, None] * cl.vel).sum(0)
     _, v, _ = oracle.leapfrog(cl.pos, cl.vel, a0, cl.mass, 1e-2, 2.0 ** -8, 32)
     assert np.abs((cl.mass[:, None] * v).sum(0) - p0).max() < 1e-13
+
+
+def test_oracle_reproduces_stored_values():
+    # tests/golden/plummer64_seed0_eps1e-2.txt, written by
+    # tests/golden/make_golden.py from the oracle: the same numbers on every
+    # host the oracle is built on (compensated sums, no FMA contraction)
+    path = os.path.join(os.path.dirname(__file__), "golden", "plummer64_seed0_eps1e-2.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    ek_ref, ep_ref = (float(t) for t in rows[0][1:])
+    force = np.array([[float(t) for t in r[1:]] for r in rows if r[0] == "force"])
+    lf = np.array([[float(t) for t in r[1:]] for r in rows if r[0] == "leapfrog8"])
+    cl = inputs.plummer(64, seed=0)
+    acc, jerk, pot = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)
+    ek, ep = oracle.energy(cl.pos, cl.vel, cl.mass, 1e-2)
+    x, v, _ = oracle.leapfrog(cl.pos, cl.vel, acc, cl.mass, 1e-2, 2.0 ** -6, 8)
+    got = np.hstack([acc, jerk, pot[:, None]])
+    assert np.allclose(got, force, rtol=1e-14, atol=1e-14)
+    assert ek == pytest.approx(ek_ref, rel=1e-14) and ep == pytest.approx(ep_ref, rel=1e-14)
+    assert np.allclose(np.hstack([x, v]), lf, rtol=1e-13, atol=1e-13)
