@@ -254,6 +254,14 @@ int nb_status(nb_ctx *ctx);
 /* Clear the sticky device status. */
 int nb_clear_status(nb_ctx *ctx);
 
+/* Self-check of the failure detection: launch one kernel whose device wait
+ * (an mbarrier phase that nothing completes) runs out after `seconds`
+ * (0 < seconds <= 10) of SM clock, exactly as a force kernel's wait for a
+ * source tile would; the sticky status becomes NB_ETIMEOUT (nb_status reads
+ * it, nb_clear_status clears it) and the context stays usable.  Nothing
+ * faults, traps or hangs.  Asynchronous. */
+int nb_check_wait_timeout(nb_ctx *ctx, double seconds);
+
 /* Text for a status code (static storage). */
 const char *nb_strerror(int code);
 

@@ -939,6 +939,16 @@ int nb_status(nb_ctx* c) {
   return sync_status(c);
 }
 
+int nb_check_wait_timeout(nb_ctx* c, double seconds) {
+  if (!c || !(seconds > 0.0) || seconds > 10.0) return NB_EINVAL;
+  int dev = 0, khz = 0;
+  NB_TRY(cudaGetDevice(&dev));
+  NB_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  const long long budget = static_cast<long long>(seconds * 1e3 * (khz > 0 ? khz : 2000000));
+  NB_TRY(launch_wait_probe(c->d.status, budget, c->st));
+  return NB_OK;
+}
+
 int nb_clear_status(nb_ctx* c) {
   if (!c) return NB_EINVAL;
   NB_TRY(cudaMemsetAsync(c->d.status, 0, 4, c->st));

@@ -769,6 +769,22 @@ __global__ void k_slot_list(Dev d) {
   }
 }
 
+// Self-check of the bounded device waits: an mbarrier phase that nothing
+// completes (one expected arrival, none made); the wait gives up after
+// `budget` clock cycles and reports it in the sticky status, as the force
+// kernels do when a bulk copy never lands.  Nothing is in flight on the
+// barrier, so the CTA simply returns.
+__global__ void k_wait_probe(uint32_t* status, long long budget) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u, budget);
+  if (!ok && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+}
+
 __global__ void k_tcur_from_t(Dev d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -795,6 +811,10 @@ cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, 
                            bool mix, bool f64, bool count_due, cudaStream_t st, bool zero_tau) {
   k_predict_tiles<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d, t_tgt, t_fixed, T, mix,
                                                                   f64, count_due, zero_tau);
+  return cudaGetLastError();
+}
+cudaError_t launch_wait_probe(uint32_t* status, long long budget, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(status, budget);
   return cudaGetLastError();
 }
 cudaError_t launch_slot_list(const Dev& d, cudaStream_t st) {

@@ -131,6 +131,9 @@ cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st);
 // zero_tau: sources at the stored positions (no Taylor step)
 cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T, bool mix,
                            bool f64, bool count_due, cudaStream_t st, bool zero_tau = false);
+// a bounded wait that nothing completes: sets the timeout bit after `budget`
+// clock cycles (the self-check behind nb_check_wait_timeout)
+cudaError_t launch_wait_probe(uint32_t* status, long long budget, cudaStream_t st);
 // every particle in source-slot order into d.active (use it as the rows too)
 cudaError_t launch_slot_list(const Dev& d, cudaStream_t st);
 // leapfrog halves (a_new == nullptr: kick + drift + time; else kick + store)

@@ -25,7 +25,7 @@ FUNCTIONS = [
     "nb_correct", "nb_step_block", "nb_set_end_time", "nb_energy", "nb_get_state",
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
     "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
-    "nb_energies", "nb_autotune", "nb_step_leapfrog",
+    "nb_energies", "nb_autotune", "nb_step_leapfrog", "nb_check_wait_timeout",
 ]
 
 
@@ -65,6 +65,7 @@ def _load() -> ctypes.CDLL:
         "nb_correct": (ctypes.c_int, [P, i64, P, i64, P, P]),
         "nb_step_block": (ctypes.c_int, [P, i64]),
         "nb_step_leapfrog": (ctypes.c_int, [P, i64, i64]),
+        "nb_check_wait_timeout": (ctypes.c_int, [P, ctypes.c_double]),
         "nb_set_end_time": (ctypes.c_int, [P, i64]),
         "nb_energy": (ctypes.c_int, [P, i32, P, P]),
         "nb_get_state": (ctypes.c_int, [P, P, P, P, P, P, P]),
@@ -304,6 +305,10 @@ class Sim:
 
     def status(self) -> int:
         return int(lib.nb_status(self._ctx))
+
+    def check_wait_timeout(self, seconds: float = 0.05):
+        """nb_check_wait_timeout: a device wait that runs out on purpose."""
+        _check(lib.nb_check_wait_timeout(self._ctx, float(seconds)), "nb_check_wait_timeout")
 
     def clear_status(self):
         _check(lib.nb_clear_status(self._ctx), "nb_clear_status")

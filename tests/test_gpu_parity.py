@@ -541,3 +541,44 @@ def test_leapfrog_mixed_matches_oracle(nb):
     assert np.all(dv <= 2 * steps * dt * 1e-6 * Sa + 1e-14)
     assert np.all(dx <= 2 * steps ** 2 * dt ** 2 * 1e-6 * Sa + 1e-14)
     assert (np.linalg.norm(s["acc"] - a, axis=1) / Sa).max() <= 2e-6
+
+
+# ------------------------------------------------- failure detection ----
+
+def test_wait_timeout_is_reported_and_context_survives(nb, plummer1024):
+    """A device wait that nothing completes runs out after its clock budget:
+    the sticky status says NB_ETIMEOUT, and after clearing it the context
+    computes forces as before."""
+    cl = plummer1024
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nb.NB_MIXED)
+    try:
+        sim.check_wait_timeout(0.05)
+        assert sim.status() == nb.NB_ETIMEOUT
+        sim.clear_status()
+        assert sim.status() == nb.NB_OK
+        sim.predict(0)
+        act = torch.arange(0, cl.n, 7, dtype=torch.int32, device="cuda")
+        a, j, p = sim.force(act)
+        torch.cuda.synchronize()
+        assert sim.status() == nb.NB_OK
+        ra, _, _ = oracle.force(cl.pos, cl.vel, cl.mass, 1e-4,
+                                idx=act.cpu().numpy().astype(np.int64))
+        assert rel_err(a.cpu().numpy(), ra).max() <= 1e-5
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_nonfinite_state_is_reported(nb, prec):
+    """Two coincident particles without softening give an infinite force; the
+    corrector finds the non-finite state and the status says NB_ENONFINITE."""
+    cl = inputs.plummer(64, seed=5)
+    pos = cl.pos.copy()
+    pos[1] = pos[0]
+    P = nb.NB_FP64 if prec == "fp64" else nb.NB_MIXED
+    sim = nb.Sim(pos, cl.vel, cl.mass, eps=0.0, precision=P, level_min=3, level_max=20)
+    try:
+        sim.step(1)
+        assert sim.status() == nb.NB_ENONFINITE
+    finally:
+        sim.close()
