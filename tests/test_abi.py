@@ -72,3 +72,38 @@ def test_precision_modes_in_config(libpath):
         assert nbody.workspace_size(1000, 1, cfg) > 0
     with pytest.raises(nbody.NBError):
         nbody.workspace_size(1000, 1, nbody.default_config(precision=4))
+
+
+def test_init_rejects_bad_workspaces_before_touching_the_device(libpath):
+    """nb_init checks its arguments and the workspace size on the host and
+    returns before any device call: too small a workspace is NB_ENOMEM (the
+    library's analogue of an allocation failure: it allocates nothing
+    itself), a misaligned one or bad particle data NB_EINVAL."""
+    import ctypes
+    import numpy as np
+    from paper_1411_5234_gb300 import nbody
+    lib = nbody.lib
+    n = 64
+    cfg = nbody.default_config()
+    pos = np.zeros((n, 3)) + np.arange(n)[:, None]
+    vel = np.zeros((n, 3))
+    mass = np.full(n, 1.0 / n)
+    off = np.array([0, n], dtype=np.int64)
+    buf = np.zeros(1 << 16, dtype=np.uint8)
+    base = buf.ctypes.data
+    aligned = (base + 255) // 256 * 256
+    need = nbody.workspace_size(n, 1, cfg)
+    ctx = ctypes.c_void_p()
+
+    def init(ptr, nbytes, m=mass, o=off):
+        return lib.nb_init(ctypes.byref(ctx), ctypes.byref(cfg), 1, o.ctypes.data_as(ctypes.c_void_p),
+                           m.ctypes.data_as(ctypes.c_void_p), pos.ctypes.data_as(ctypes.c_void_p),
+                           vel.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ptr), nbytes, None)
+
+    assert need > 4096
+    assert init(aligned, 4096) == nbody.NB_ENOMEM
+    assert init(aligned + 8, need) == nbody.NB_EINVAL          # misaligned
+    assert init(aligned, 4096, m=-mass) == nbody.NB_EINVAL     # negative masses
+    bad_off = np.array([0, 0], dtype=np.int64)
+    assert init(aligned, 4096, o=bad_off) == nbody.NB_EINVAL   # empty cluster
+    assert not ctx.value
