@@ -10,12 +10,24 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nbody_gb300.h"
 #include "nb_integrator.cuh"
 
 using namespace nb;
 
 namespace {
+
+// Host-side NVTX range around an ABI call (the span in which it enqueues its
+// work, or waits for it when the call synchronises); a no-op unless a
+// profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr size_t kAlign = 256;
 constexpr int kEnergyBlocks = 304;
@@ -430,6 +442,7 @@ int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config* cfg,
 int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_t* offsets,
             const double* mass, const double* pos, const double* vel, void* workspace,
             size_t workspace_bytes, void* stream) {
+  NvtxRange nvtx_range("nb_init");
   if (!out || !config_ok(cfg) || n_clusters < 1 || !offsets || !mass || !pos || !vel ||
       !workspace)
     return NB_EINVAL;
@@ -596,6 +609,7 @@ void nb_free(nb_ctx* c) {
 }
 
 int nb_predict(nb_ctx* c, int64_t t_ticks) {
+  NvtxRange nvtx_range("nb_predict");
   if (!c || t_ticks < 0) return NB_EINVAL;
   const bool f64 = !is_mixed(c);
   NB_TRY(launch_predict(c->d, nullptr, t_ticks, c->cfg.tick_exp, !f64, f64, false, c->st));
@@ -604,6 +618,7 @@ int nb_predict(nb_ctx* c, int64_t t_ticks) {
 
 int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, double* jerk,
              double* pot) {
+  NvtxRange nvtx_range("nb_force");
   if (!c || m < 0 || m > c->d.N) return NB_EINVAL;
   if (m == 0) return NB_OK;
   if (!active_idx || !acc) return NB_EINVAL;
@@ -616,6 +631,7 @@ int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, doubl
 
 int nb_correct(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
                const double* acc, const double* jerk) {
+  NvtxRange nvtx_range("nb_correct");
   if (!c || m < 0 || m > c->d.N || t_ticks < 0) return NB_EINVAL;
   if (m == 0) return NB_OK;
   if (!active_idx || !acc || !jerk) return NB_EINVAL;
@@ -639,6 +655,7 @@ int nb_correct(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
 }
 
 int nb_step_leapfrog(nb_ctx* c, int64_t n_steps, int64_t dt_ticks) {
+  NvtxRange nvtx_range("nb_step_leapfrog");
   if (!c || n_steps < 0 || dt_ticks <= 0 || dt_ticks > ((int64_t)1 << 52)) return NB_EINVAL;
   if (n_steps == 0) return NB_OK;
   const bool f64 = !is_mixed(c);
@@ -661,6 +678,7 @@ int nb_step_leapfrog(nb_ctx* c, int64_t n_steps, int64_t dt_ticks) {
 }
 
 int nb_step_block(nb_ctx* c, int64_t n_steps) {
+  NvtxRange nvtx_range("nb_step_block");
   if (!c || n_steps < 0) return NB_EINVAL;
   const int G = c->cfg.graph_steps;
   const bool graphs = G > 0 && c->st != nullptr && !c->graph_broken && !c->prof;
@@ -699,6 +717,7 @@ int nb_set_end_time(nb_ctx* c, int64_t t_end_ticks) {
 }
 
 int nb_energy(nb_ctx* c, int32_t cluster, double* ekin, double* epot) {
+  NvtxRange nvtx_range("nb_energy");
   if (!c || !ekin || !epot || cluster < -1 || cluster >= c->d.K) return NB_EINVAL;
   Dev& d = c->d;
   double* an = reinterpret_cast<double*>(d.acc_new);
@@ -720,6 +739,7 @@ int nb_energy(nb_ctx* c, int32_t cluster, double* ekin, double* epot) {
 }
 
 int nb_energies(nb_ctx* c, double* ekin, double* epot) {
+  NvtxRange nvtx_range("nb_energies");
   if (!c || !ekin || !epot) return NB_EINVAL;
   Dev& d = c->d;
   double* an = reinterpret_cast<double*>(d.acc_new);
@@ -746,6 +766,7 @@ int nb_energies(nb_ctx* c, double* ekin, double* epot) {
 
 int nb_get_state(nb_ctx* c, double* pos, double* vel, double* acc, double* jerk, int64_t* t,
                  int32_t* level) {
+  NvtxRange nvtx_range("nb_get_state");
   if (!c) return NB_EINVAL;
   const int64_t N = c->d.N;
   // pack (n, 3) rows into the step scratch (acc_new / jerk_new), then copy
@@ -771,6 +792,7 @@ int nb_get_state(nb_ctx* c, double* pos, double* vel, double* acc, double* jerk,
 
 int nb_set_state(nb_ctx* c, const double* pos, const double* vel, const double* acc,
                  const double* jerk, const int64_t* t, const int32_t* level) {
+  NvtxRange nvtx_range("nb_set_state");
   if (!c || !pos || !vel || !acc || !jerk || !t || !level) return NB_EINVAL;
   const int64_t N = c->d.N;
   const int T = c->cfg.tick_exp;
@@ -847,6 +869,7 @@ int nb_tile_stats(nb_ctx* c, int64_t* warp_tiles, int64_t* near_warp_tiles) {
 }
 
 int nb_autotune(nb_ctx* c, int32_t* variant_out, double* ms_out) {
+  NvtxRange nvtx_range("nb_autotune");
   if (!c) return NB_EINVAL;
   if (c->cfg.precision != NB_MIXED) {  // FP64, DS, FP32: one shape each, nothing to choose
     if (variant_out) *variant_out = c->cfg.variant;
