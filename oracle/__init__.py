@@ -79,6 +79,14 @@ def _load():
         lib.oracle_drift.restype = None
         lib.oracle_leapfrog.argtypes = [i64, P, P, P, P, f64, f64, f64, i64]
         lib.oracle_leapfrog.restype = i32
+        lib.oracle_force_snap.argtypes = [i64, P, P, P, P, f64, f64, i64, P, P, P, P]
+        lib.oracle_force_snap.restype = i32
+        lib.oracle_hermite6_correct.argtypes = [i64] + [P] * 14
+        lib.oracle_hermite6_correct.restype = None
+        lib.oracle_hermite6_dt.argtypes = [P, P, P, P, P, P, f64]
+        lib.oracle_hermite6_dt.restype = f64
+        lib.oracle_hermite6_run.argtypes = [i64, P, P, P, f64, f64, f64, i64]
+        lib.oracle_hermite6_run.restype = i32
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = i32
         lib.oracle_set_threads.argtypes = [i32]
@@ -232,6 +240,56 @@ def leapfrog(pos, vel, acc, mass, eps, dt, n_steps, G=1.0):
     if rc != 0:
         raise MemoryError("oracle_leapfrog")
     return pos, vel, acc
+
+
+def force_snap(pos, vel, acc, mass, eps, idx=None, G=1.0):
+    """Acceleration, jerk and snap of targets ``idx`` (the 6th-order scheme's
+    force), from positions, velocities and accelerations of all particles.
+    Returns ``(acc, jerk, snap)``, each (m, 3)."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    vel, acc = _f64(vel, (n, 3)), _f64(acc, (n, 3))
+    mass = _f64(mass, (n,))
+    idx = np.arange(n, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, np.int64)
+    m = idx.shape[0]
+    out = [np.empty((m, 3)) for _ in range(3)]
+    rc = _load().oracle_force_snap(n, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(mass), float(G),
+                                   float(eps), m, _ptr(idx), *[_ptr(o) for o in out])
+    if rc != 0:
+        raise ValueError("oracle_force_snap: target index out of range")
+    return tuple(out)
+
+
+def hermite6_correct(h, x0, v0, a0, j0, s0, a1, j1, s1):
+    """6th-order Hermite corrector.  Returns ``(x1, v1, crackle, pop, a5)``
+    (the last three: the interpolant's derivatives at the end)."""
+    x0 = _f64(x0).reshape(-1, 3)
+    m = x0.shape[0]
+    args = [_f64(a, (m, 3)) for a in (v0, a0, j0, s0, a1, j1, s1)]
+    h = _f64(np.broadcast_to(np.asarray(h, dtype=np.float64), (m,)))
+    out = [np.empty((m, 3)) for _ in range(5)]
+    _load().oracle_hermite6_correct(m, _ptr(h), _ptr(x0), *[_ptr(a) for a in args],
+                                    *[_ptr(o) for o in out])
+    return tuple(out)
+
+
+def hermite6_dt(a, j, s, c, p, q, eta):
+    """Step criterion of the 6th-order scheme (generalised Aarseth, p = 6)."""
+    vs = [_f64(x, (3,)) for x in (a, j, s, c, p, q)]
+    return float(_load().oracle_hermite6_dt(*[_ptr(x) for x in vs], float(eta)))
+
+
+def hermite6_run(pos, vel, mass, eps, h, n_steps, G=1.0):
+    """Shared-step 6th-order Hermite integration; returns ``(pos, vel)``."""
+    pos = _f64(pos).reshape(-1, 3).copy()
+    n = pos.shape[0]
+    vel = _f64(vel, (n, 3)).copy()
+    mass = _f64(mass, (n,))
+    rc = _load().oracle_hermite6_run(n, _ptr(pos), _ptr(vel), _ptr(mass), float(G),
+                                     float(eps), float(h), int(n_steps))
+    if rc != 0:
+        raise MemoryError("oracle_hermite6_run")
+    return pos, vel
 
 
 class State:

@@ -477,3 +477,192 @@ int oracle_leapfrog(int64_t n, double *pos, double *vel, double *acc,
     free(idx);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* 6th-order Hermite scheme (the order of the paper's template code,    */
+/* Sec. 2 item 1; the paper prints no formula for it).                  */
+/*                                                                      */
+/* Force with snap.  With d = r_j - r_i, w = v_j - v_i, u = a_j - a_i   */
+/* (the sources' and the target's accelerations at the same time),     */
+/* s^2 = d.d + eps^2, alpha = (d.w)/s^2 and                             */
+/* beta = (w.w + d.u)/s^2 + alpha^2, the pair term of Eq. 2 and its     */
+/* first two time derivatives are                                       */
+/*   A = G m_j d / s^3,                                                 */
+/*   J = G m_j w / s^3 - 3 alpha A,                                     */
+/*   S = G m_j u / s^3 - 6 alpha J - 3 beta A                           */
+/* (differentiate A in time twice; d(alpha)/dt = beta - 3 alpha^2).     */
+/* acc_src: n x 3 accelerations of all particles (the sources' and the  */
+/* targets' own); out: acc, jerk, snap (m x 3), Neumaier-summed.        */
+/* Returns 0, or -1 on a bad index.                                     */
+/* ------------------------------------------------------------------ */
+int oracle_force_snap(int64_t n, const double *pos, const double *vel,
+                      const double *acc_src, const double *mass, double G,
+                      double eps, int64_t m, const int64_t *idx, double *acc,
+                      double *jerk, double *snap)
+{
+    for (int64_t k = 0; k < m; k++)
+        if (idx[k] < 0 || idx[k] >= n) return -1;
+    const double eps2 = eps * eps;
+    int64_t k;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (k = 0; k < m; k++) {
+        const int64_t i = idx[k];
+        nsum sa[3], sj[3], ss[3];
+        memset(sa, 0, sizeof sa);
+        memset(sj, 0, sizeof sj);
+        memset(ss, 0, sizeof ss);
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double d[3], w[3], u[3];
+            for (int c = 0; c < 3; c++) {
+                d[c] = pos[3 * j + c] - pos[3 * i + c];
+                w[c] = vel[3 * j + c] - vel[3 * i + c];
+                u[c] = acc_src[3 * j + c] - acc_src[3 * i + c];
+            }
+            double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+            double s3 = s2 * sqrt(s2);
+            double dw = d[0] * w[0] + d[1] * w[1] + d[2] * w[2];
+            double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+            double du = d[0] * u[0] + d[1] * u[1] + d[2] * u[2];
+            double alpha = dw / s2;
+            double beta = (ww + du) / s2 + alpha * alpha;
+            double gm = G * mass[j];
+            for (int c = 0; c < 3; c++) {
+                double A = gm * d[c] / s3;
+                double J = gm * w[c] / s3 - 3.0 * alpha * A;
+                double S = gm * u[c] / s3 - 6.0 * alpha * J - 3.0 * beta * A;
+                nsum_add(&sa[c], A);
+                nsum_add(&sj[c], J);
+                nsum_add(&ss[c], S);
+            }
+        }
+        for (int c = 0; c < 3; c++) {
+            if (acc) acc[3 * k + c] = nsum_get(&sa[c]);
+            if (jerk) jerk[3 * k + c] = nsum_get(&sj[c]);
+            if (snap) snap[3 * k + c] = nsum_get(&ss[c]);
+        }
+    }
+    return 0;
+}
+
+/* 6th-order Hermite corrector over a step h, from (x0, v0, a0, j0, s0) */
+/* at the start and the force (a1, j1, s1) at the predicted end: the    */
+/* quintic through (a0, j0, s0) and (a1, j1, s1) integrates exactly to   */
+/*   v1 = v0 + h/2 (a0 + a1) - h^2/10 (j1 - j0) + h^3/120 (s0 + s1),     */
+/* and the same rule on v (derivatives a, j) gives                      */
+/*   x1 = x0 + h/2 (v0 + v1) - h^2/10 (a1 - a0) + h^3/120 (j0 + j1).     */
+/* The quintic's derivatives at the end, for the next prediction and    */
+/* the step criterion (Delta = a1 - a0):                                */
+/*   crackle h^3 = 60 Delta - h (24 j0 + 36 j1) - h^2 (3 s0 - 9 s1),     */
+/*   pop h^4     = 360 Delta - h (168 j0 + 192 j1) - h^2 (24 s0 - 36 s1),*/
+/*   a5 h^5      = 720 Delta - 360 h (j0 + j1) - 60 h^2 (s0 - s1).       */
+/* m particles, all arrays m x 3; h per particle.                       */
+/* ------------------------------------------------------------------ */
+void oracle_hermite6_correct(int64_t m, const double *h, const double *x0,
+                             const double *v0, const double *a0,
+                             const double *j0, const double *s0,
+                             const double *a1, const double *j1,
+                             const double *s1, double *x1, double *v1,
+                             double *crackle, double *pop, double *a5)
+{
+    for (int64_t k = 0; k < m; k++) {
+        const double t = h[k], t2 = t * t, t3 = t2 * t;
+        for (int q = 0; q < 3; q++) {
+            const int64_t i = 3 * k + q;
+            /* every input is read before any output is written: the
+               outputs may alias the inputs (x1 = x0, v1 = v0) */
+            const double xo = x0[i], vo = v0[i];
+            const double vv = vo + t / 2.0 * (a0[i] + a1[i])
+                              - t2 / 10.0 * (j1[i] - j0[i])
+                              + t3 / 120.0 * (s0[i] + s1[i]);
+            const double xx = xo + t / 2.0 * (vo + vv)
+                              - t2 / 10.0 * (a1[i] - a0[i])
+                              + t3 / 120.0 * (j0[i] + j1[i]);
+            v1[i] = vv;
+            x1[i] = xx;
+            const double D = a1[i] - a0[i];
+            if (crackle)
+                crackle[i] = (60.0 * D - t * (24.0 * j0[i] + 36.0 * j1[i])
+                              - t2 * (3.0 * s0[i] - 9.0 * s1[i])) / t3;
+            if (pop)
+                pop[i] = (360.0 * D - t * (168.0 * j0[i] + 192.0 * j1[i])
+                          - t2 * (24.0 * s0[i] - 36.0 * s1[i])) / (t3 * t);
+            if (a5)
+                a5[i] = (720.0 * D - 360.0 * t * (j0[i] + j1[i])
+                         - 60.0 * t2 * (s0[i] - s1[i])) / (t3 * t2);
+        }
+    }
+}
+
+/* Step criterion of the 6th-order scheme: the generalised Aarseth      */
+/* form of the p-th order Hermite schemes at p = 6,                     */
+/*   dt = eta ( A1 / A4 )^(1/3),  A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)|, */
+/* with a^(0..5) = a, jerk, snap, crackle, pop, a5; zero denominator    */
+/* gives +inf.                                                          */
+/* ------------------------------------------------------------------ */
+double oracle_hermite6_dt(const double *a, const double *j, const double *s,
+                          const double *c, const double *p, const double *q,
+                          double eta)
+{
+    const double na = norm3(a), nj = norm3(j), ns = norm3(s);
+    const double nc = norm3(c), np_ = norm3(p), nq = norm3(q);
+    const double A1 = sqrt(na * ns) + nj;
+    const double A4 = sqrt(nc * nq) + np_;
+    if (!(A4 > 0.0)) return INFINITY;
+    return eta * cbrt(A1 / A4);
+}
+
+/* Shared-step 6th-order Hermite integration of every particle: n_steps */
+/* steps of h.  Start: acc and jerk from oracle_force, snap from        */
+/* oracle_force_snap with those accelerations, crackle zero (the first  */
+/* prediction lacks its c tau^5/120 term; one step's error, so the      */
+/* scheme stays 6th order).  Per step: predict every particle with      */
+/*   x_p = x + v t + a t^2/2 + j t^3/6 + s t^4/24 + c t^5/120,          */
+/*   v_p = v + a t + j t^2/2 + s t^3/6 + c t^4/24,                      */
+/*   a_p = a + j t + s t^2/2 + c t^3/6,                                 */
+/* take the force with snap at (x_p, v_p, a_p) and correct.             */
+/* Returns 0, or -1 when memory runs out.                               */
+/* ------------------------------------------------------------------ */
+int oracle_hermite6_run(int64_t n, double *pos, double *vel,
+                        const double *mass, double G, double eps, double h,
+                        int64_t n_steps)
+{
+    const size_t b = sizeof(double) * 3 * (size_t)(n > 0 ? n : 1);
+    double *a = malloc(b), *j = malloc(b), *s = malloc(b), *c = malloc(b);
+    double *xp = malloc(b), *vp = malloc(b), *ap = malloc(b);
+    double *a1 = malloc(b), *j1 = malloc(b), *s1 = malloc(b);
+    double *hh = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int64_t *idx = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int rc = 0;
+    if (!a || !j || !s || !c || !xp || !vp || !ap || !a1 || !j1 || !s1 || !hh || !idx) {
+        rc = -1;
+        goto done;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        idx[i] = i;
+        hh[i] = h;
+    }
+    oracle_force(n, pos, vel, mass, G, eps, n, idx, a, j, NULL);
+    oracle_force_snap(n, pos, vel, a, mass, G, eps, n, idx, NULL, NULL, s);
+    memset(c, 0, b);
+    for (int64_t st = 0; st < n_steps; st++) {
+        const double t = h, t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
+        for (int64_t i = 0; i < 3 * n; i++) {
+            xp[i] = pos[i] + vel[i] * t + a[i] * t2 / 2.0 + j[i] * t3 / 6.0
+                    + s[i] * t4 / 24.0 + c[i] * t5 / 120.0;
+            vp[i] = vel[i] + a[i] * t + j[i] * t2 / 2.0 + s[i] * t3 / 6.0
+                    + c[i] * t4 / 24.0;
+            ap[i] = a[i] + j[i] * t + s[i] * t2 / 2.0 + c[i] * t3 / 6.0;
+        }
+        oracle_force_snap(n, xp, vp, ap, mass, G, eps, n, idx, a1, j1, s1);
+        oracle_hermite6_correct(n, hh, pos, vel, a, j, s, a1, j1, s1, pos, vel,
+                                c, NULL, NULL);
+        memcpy(a, a1, b);
+        memcpy(j, j1, b);
+        memcpy(s, s1, b);
+    }
+done:
+    free(a); free(j); free(s); free(c); free(xp); free(vp); free(ap);
+    free(a1); free(j1); free(s1); free(hh); free(idx);
+    return rc;
+}

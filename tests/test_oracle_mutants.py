@@ -19,12 +19,15 @@ SRC = os.path.join(ROOT, "oracle", "nbody_oracle.c")
 MUTANTS = {
     "jerk_drops_3dw_term": ("gm * (w[c] / s3 - 3.0 * dw * d[c] / s5)", "gm * (w[c] / s3)"),
     "jerk_wrong_coefficient": ("gm * (w[c] / s3 - 3.0 * dw * d[c] / s5)", "gm * (w[c] / s3 - 2.0 * dw * d[c] / s5)"),
-    "separation_sign": ("d[c] = pos[3 * j + c] - pos[3 * i + c];", "d[c] = pos[3 * i + c] - pos[3 * j + c];"),
-    "velocity_transposed": ("w[c] = vel[3 * j + c] - vel[3 * i + c];", "w[c] = vel[3 * i + c] - vel[3 * j + c];"),
+    "separation_sign": ("double d[3], w[3];\n            for (int c = 0; c < 3; c++) {\n                d[c] = pos[3 * j + c] - pos[3 * i + c];",
+                        "double d[3], w[3];\n            for (int c = 0; c < 3; c++) {\n                d[c] = pos[3 * i + c] - pos[3 * j + c];"),
+    "velocity_transposed": ("w[c] = vel[3 * j + c] - vel[3 * i + c];\n            }\n            double s2",
+                            "w[c] = vel[3 * i + c] - vel[3 * j + c];\n            }\n            double s2"),
     "force_exponent": ("double s3 = s2 * s;", "double s3 = s2;"),
-    "softening_dropped": ("d[2] * d[2] + eps2;", "d[2] * d[2];"),
+    "softening_dropped": ("d[2] * d[2] + eps2;\n            double s = sqrt(s2);", "d[2] * d[2];\n            double s = sqrt(s2);"),
     "potential_sign": ("nsum_add(&p, -gm / s);", "nsum_add(&p, gm / s);"),
-    "self_term_kept": ("if (j == i) continue;", "if (j == i && eps == 0.0) continue;"),
+    "self_term_kept": ("if (j == i) continue;\n            double d[3], w[3];\n",
+                       "if (j == i && eps == 0.0) continue;\n            double d[3], w[3];\n"),
     "predictor_jerk_coefficient": ("jerk[q] * t * t * t / 6.0", "jerk[q] * t * t * t / 2.0"),
     "predictor_velocity_term": ("vp[q] = vel[q] + acc[q] * t + jerk[q] * t * t / 2.0;", "vp[q] = vel[q] + acc[q] * t;"),
     "corrector_a2_swapped": ("t * (4.0 * j0[q] + 2.0 * j1[q])", "t * (2.0 * j0[q] + 4.0 * j1[q])"),
@@ -42,6 +45,13 @@ MUTANTS = {
     "leapfrog_full_kick": ("const double h = 0.5 * dt;", "const double h = dt;"),
     "leapfrog_second_kick_dropped": ("""        oracle_force(n, pos, vel, mass, G, eps, n, idx, acc, NULL, NULL);
         oracle_kick(n, vel, acc, h);""", """        oracle_force(n, pos, vel, mass, G, eps, n, idx, acc, NULL, NULL);"""),
+    "snap_alpha_coefficient": ("- 6.0 * alpha * J - 3.0 * beta * A", "- 3.0 * alpha * J - 3.0 * beta * A"),
+    "snap_beta_without_alpha2": ("double beta = (ww + du) / s2 + alpha * alpha;", "double beta = (ww + du) / s2;"),
+    "snap_target_acceleration_dropped": ("u[c] = acc_src[3 * j + c] - acc_src[3 * i + c];", "u[c] = acc_src[3 * j + c];"),
+    "hermite6_corrector_h2_coefficient": ("- t2 / 10.0 * (j1[i] - j0[i])", "- t2 / 12.0 * (j1[i] - j0[i])"),
+    "hermite6_crackle_coefficient": ("crackle[i] = (60.0 * D", "crackle[i] = (30.0 * D"),
+    "hermite6_predictor_crackle_dropped": ("+ s[i] * t4 / 24.0 + c[i] * t5 / 120.0;", "+ s[i] * t4 / 24.0;"),
+    "hermite6_dt_exponent": ("return eta * cbrt(A1 / A4);", "return eta * sqrt(A1 / A4);"),
     "leapfrog_drift_before_kick": ("""        oracle_kick(n, vel, acc, h);
         oracle_drift(n, pos, vel, dt);""", """        oracle_drift(n, pos, vel, dt);
         oracle_kick(n, vel, acc, h);"""),

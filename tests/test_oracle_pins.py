@@ -468,3 +468,94 @@ def test_oracle_reproduces_stored_values():
     assert np.allclose(got, force, rtol=1e-14, atol=1e-14)
     assert ek == pytest.approx(ek_ref, rel=1e-14) and ep == pytest.approx(ep_ref, rel=1e-14)
     assert np.allclose(np.hstack([x, v]), lf, rtol=1e-13, atol=1e-13)
+
+
+# ------------------------------------------- 6th-order Hermite scheme ----
+
+def test_snap_is_time_derivative_of_jerk():
+    # every particle moves with its own constant acceleration u_i:
+    # x(t) = x0 + v0 t + u t^2/2, v(t) = v0 + u t; the snap at t = 0 (with
+    # the accelerations u) is d/dt of the jerk along that motion
+    rng = np.random.default_rng(3)
+    n = 12
+    x0, v0, u = rng.normal(size=(n, 3)), rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    mass = rng.uniform(0.5, 1.5, n)
+    eps = 0.1
+    h = 1e-3
+    jt = lambda t: oracle.force(x0 + v0 * t + u * t * t / 2, v0 + u * t, mass, eps)[1]
+    fd = (8 * (jt(h) - jt(-h)) - (jt(2 * h) - jt(-2 * h))) / (12 * h)
+    _, _, snap = oracle.force_snap(x0, v0, u, mass, eps)
+    assert np.allclose(snap, fd, rtol=1e-7, atol=1e-7 * np.abs(snap).max())
+
+
+def test_snap_circular_orbit_closed_form():
+    # two bodies on a circular orbit about their centre of mass: every
+    # derivative rotates with the orbit, a = -w^2 r, jerk = -w^2 v,
+    # snap = w^4 r (r, v each body's from the centre of mass)
+    m1, m2, R = 0.7, 0.3, 1.3
+    w = math.sqrt((m1 + m2) / R ** 3)
+    r1, r2 = np.array([-m2 / (m1 + m2) * R, 0, 0]), np.array([m1 / (m1 + m2) * R, 0, 0])
+    v1, v2 = np.array([0, w * r1[0], 0]), np.array([0, w * r2[0], 0])   # w z x r
+    pos, vel, mass = np.array([r1, r2]), np.array([v1, v2]), np.array([m1, m2])
+    a = -w * w * pos
+    acc, jerk, snap = oracle.force_snap(pos, vel, a, mass, 0.0)
+    assert np.allclose(acc, a, rtol=1e-13, atol=1e-15)
+    assert np.allclose(jerk, -w * w * vel, rtol=1e-13, atol=1e-15)
+    assert np.allclose(snap, w ** 4 * pos, rtol=1e-12, atol=1e-15)
+
+
+def test_snap_third_law():
+    cl = inputs.plummer(80, seed=9, imf="kroupa")
+    a = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)[0]
+    _, _, snap = oracle.force_snap(cl.pos, cl.vel, a, cl.mass, 1e-2)
+    scale = (cl.mass[:, None] * np.abs(snap)).sum(0).max()
+    assert np.abs((cl.mass[:, None] * snap).sum(0)).max() < 1e-13 * scale
+
+
+def test_hermite6_corrector_exact_for_polynomials():
+    # a degree-6 trajectory has a degree-4 acceleration, which the quintic
+    # through (a, jerk, snap) at both ends reproduces: positions, velocities
+    # and the end derivatives come out exactly (to rounding)
+    rng = np.random.default_rng(8)
+    P = rng.normal(size=(7, 3))                  # x(t) = sum_k P_k t^k
+    def deriv(t, d):
+        out = np.zeros(3)
+        for k in range(d, 7):
+            out += P[k] * math.factorial(k) / math.factorial(k - d) * t ** (k - d)
+        return out
+    h = 0.37
+    x1, v1, c1, p1, q1 = oracle.hermite6_correct(
+        h, deriv(0, 0), deriv(0, 1), deriv(0, 2), deriv(0, 3), deriv(0, 4),
+        deriv(h, 2), deriv(h, 3), deriv(h, 4))
+    assert np.allclose(x1[0], deriv(h, 0), rtol=1e-13, atol=1e-13)
+    assert np.allclose(v1[0], deriv(h, 1), rtol=1e-13, atol=1e-13)
+    assert np.allclose(c1[0], deriv(h, 5), rtol=1e-10, atol=1e-10)
+    assert np.allclose(p1[0], deriv(h, 6), rtol=1e-9, atol=1e-9)
+    assert np.allclose(q1[0], 0.0, atol=1e-8)    # the 7th derivative of x is zero
+
+
+def test_hermite6_sixth_order_kepler():
+    # closed-form Kepler orbit (e = 0.5, one period), shared steps: halving
+    # dt cuts the error by ~2^6
+    M = 4 * math.pi ** 2
+    m1, m2 = 0.6 * M, 0.4 * M
+    xk, vk = _kepler_state(1.0, 0.5, M, 0.0)
+    pos = np.array([-m2 / M * xk, m1 / M * xk])
+    vel = np.array([-m2 / M * vk, m1 / M * vk])
+    xr, _ = _kepler_state(1.0, 0.5, M, 1.0)
+    errs = []
+    for L in (7, 8, 9):
+        x, _ = oracle.hermite6_run(pos, vel, np.array([m1, m2]), 0.0, 2.0 ** -L, 2 ** L)
+        errs.append(np.linalg.norm((x[1] - x[0]) - xr))
+    assert errs[0] < 1e-4
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 48.0 < e1 / e2 < 80.0, errs
+
+
+def test_hermite6_dt_circular_orbit():
+    # on a circular orbit |a^(k)| = w^k |a|, so A1 = 2 w |a| ... the
+    # generalised criterion gives eta / w exactly
+    w, r = 2.5, 0.8
+    vecs = [np.array([math.cos(0.3 + k * math.pi / 2), math.sin(0.3 + k * math.pi / 2), 0.0])
+            * r * w ** (k + 2) for k in range(6)]
+    assert oracle.hermite6_dt(*vecs, 0.2) == pytest.approx(0.2 / w, rel=1e-14)
