@@ -425,7 +425,8 @@ int oracle_init(int64_t n, const double *pos, const double *vel,
                 int32_t *level, double G, double eps, double eta_s,
                 int tick_exp, int lmin, int lmax)
 {
-    int64_t *all = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *all = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    if (!all) return -1;
     for (int64_t i = 0; i < n; i++) all[i] = i;
     int rc = oracle_force(n, pos, vel, mass, G, eps, n, all, acc, jerk, NULL);
     free(all);
