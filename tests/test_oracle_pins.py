@@ -559,3 +559,50 @@ def test_hermite6_dt_circular_orbit():
     vecs = [np.array([math.cos(0.3 + k * math.pi / 2), math.sin(0.3 + k * math.pi / 2), 0.0])
             * r * w ** (k + 2) for k in range(6)]
     assert oracle.hermite6_dt(*vecs, 0.2) == pytest.approx(0.2 / w, rel=1e-14)
+
+
+# --------------------------------------------------------- symmetries ----
+
+def _rotation(seed):
+    q = np.random.default_rng(seed).normal(size=4)
+    a, b, c, d = q / np.linalg.norm(q)
+    return np.array([[a*a + b*b - c*c - d*d, 2*(b*c - a*d), 2*(b*d + a*c)],
+                     [2*(b*c + a*d), a*a - b*b + c*c - d*d, 2*(c*d - a*b)],
+                     [2*(b*d - a*c), 2*(c*d + a*b), a*a - b*b - c*c + d*d]])
+
+
+def test_force_translation_and_rotation_covariance():
+    cl = inputs.plummer(50, seed=21, imf="kroupa")
+    a, j, p = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)
+    sa, sj = np.abs(a).max(), np.abs(j).max()
+    a2, j2, p2 = oracle.force(cl.pos + np.array([3.0, -7.0, 11.0]), cl.vel, cl.mass, 1e-2)
+    assert np.allclose(a2, a, rtol=0, atol=1e-12 * sa) and np.allclose(j2, j, rtol=0, atol=1e-12 * sj)
+    assert np.allclose(p2, p, rtol=1e-12)
+    R = _rotation(4)
+    a3, j3, p3 = oracle.force(cl.pos @ R.T, cl.vel @ R.T, cl.mass, 1e-2)
+    assert np.allclose(a3, a @ R.T, rtol=0, atol=1e-13 * sa)
+    assert np.allclose(j3, j @ R.T, rtol=0, atol=1e-13 * sj)
+    assert np.allclose(p3, p, rtol=1e-13)
+
+
+def test_force_galilean_reversal_and_mass_scaling():
+    cl = inputs.plummer(50, seed=22, imf="kroupa")
+    a, j, p = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)
+    sj = np.abs(j).max()
+    # a common velocity changes no relative velocity: acc and jerk stay
+    a2, j2, _ = oracle.force(cl.pos, cl.vel + np.array([5.0, -2.0, 1.0]), cl.mass, 1e-2)
+    assert np.array_equal(a2, a) and np.allclose(j2, j, rtol=0, atol=1e-12 * sj)
+    # reversed velocities: acc stays, the jerk flips
+    a3, j3, _ = oracle.force(cl.pos, -cl.vel, cl.mass, 1e-2)
+    assert np.array_equal(a3, a) and np.allclose(j3, -j, rtol=0, atol=1e-14 * sj)
+    # twice the masses: twice every sum
+    a4, j4, p4 = oracle.force(cl.pos, cl.vel, 2.0 * cl.mass, 1e-2)
+    assert np.allclose(a4, 2 * a, rtol=1e-14) and np.allclose(p4, 2 * p, rtol=1e-14)
+
+
+def test_snap_invariant_under_a_common_acceleration():
+    cl = inputs.plummer(40, seed=23)
+    acc = oracle.force(cl.pos, cl.vel, cl.mass, 1e-2)[0]
+    _, _, s1 = oracle.force_snap(cl.pos, cl.vel, acc, cl.mass, 1e-2)
+    _, _, s2 = oracle.force_snap(cl.pos, cl.vel, acc + np.array([0.3, 0.1, -0.2]), cl.mass, 1e-2)
+    assert np.allclose(s2, s1, rtol=0, atol=1e-12 * np.abs(s1).max())
