@@ -107,3 +107,15 @@ def test_init_rejects_bad_workspaces_before_touching_the_device(libpath):
     bad_off = np.array([0, 0], dtype=np.int64)
     assert init(aligned, 4096, o=bad_off) == nbody.NB_EINVAL   # empty cluster
     assert not ctx.value
+
+
+def test_workspace_memory_model(libpath):
+    """~557 B per particle at large N in one workspace (both source layouts,
+    partial sums, maps): N = 2^20 fits in 0.6 GB, 280 GB hold ~5e8."""
+    from paper_1411_5234_gb300 import nbody
+    cfg = nbody.default_config()
+    per = [nbody.workspace_size(n, 1, cfg) / n for n in (1 << 20, 1 << 24)]
+    assert all(500 < p < 620 for p in per), per
+    assert nbody.workspace_size(1 << 20, 1, cfg) < 0.6e9
+    # many small clusters cost a little more per particle (per-cluster tiles)
+    assert nbody.workspace_size(2007990, 512, cfg) / 2007990 < 620
