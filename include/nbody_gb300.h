@@ -37,7 +37,7 @@
  *              (the offsets' low words unused): the speed bound, whose
  *              separation error is relative to the cell size rather than to
  *              the separation, so close pairs lose accuracy.
- *   NB_DS and NB_FP32 use the 64 x 4 kernel shape (variant 2); nb_force
+ *   NB_DS and NB_FP32 use the default kernel shape (variant 0); nb_force
  *   without jerk uses the mixed separations in every non-FP64 mode.
  *
  * Memory ownership
@@ -106,7 +106,7 @@ typedef struct {
 
 /* Defaults: G = 1, eps = 1e-4, eta = 0.01, eta_start = 0.01, level_min = 0,
  * level_max = 30, tick_exp = 40, NB_MIXED, bfactor = 0, graph_steps = 16,
- * sort_sources = 1, variant = 2. */
+ * sort_sources = 1, variant = 0. */
 void nb_default_config(nb_config *cfg);
 
 /* Bytes of the device workspace for n_total particles in n_clusters clusters
@@ -275,7 +275,9 @@ const char *nb_strerror(int code);
  * pos, vel (n x 3), mass (n), target_idx (m int32 in [0, n), any order),
  * outputs acc, jerk (m x 3) and pot (m, or NULL), on `stream`.
  * precision is NB_MIXED or NB_FP64.  Asynchronous; a target index outside
- * [0, n) leaves its row unspecified.
+ * [0, n) leaves its row unspecified and sets the status that
+ * nb_noalloc_status() reports, as does a device wait that gave up (its rows
+ * are then unspecified too).
  *
  * It allocates nothing: the packed sources, the i-split partial sums and the
  * plan words live in one fixed device array of 6,705,664 bytes compiled into
@@ -292,6 +294,15 @@ int nb_force_noalloc(const double *pos, const double *vel, const double *mass,
                      int64_t n, const int32_t *target_idx, int64_t m, double G,
                      double eps, int32_t precision, double *acc, double *jerk,
                      double *pot, void *stream);
+
+/* Device status of the last nb_force_noalloc call enqueued on `stream` on the
+ * current device: NB_OK, NB_EINVAL (a target index outside [0, n)),
+ * NB_ETIMEOUT (a device wait gave up) or NB_ECUDA.  Every call starts from a
+ * cleared status, so the answer covers that one call, provided no call on
+ * another stream of the device ran in between (calls share the fixed array).
+ * Copies one word from the fixed array and synchronises `stream`; allocates
+ * nothing. */
+int nb_noalloc_status(void *stream);
 
 #ifdef __cplusplus
 }

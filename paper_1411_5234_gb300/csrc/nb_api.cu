@@ -35,7 +35,7 @@ constexpr int kEnergyBlocks = 304;
 struct Layout {
   size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
       src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, wt_off, wide_cnt, bfac, esum,
-      status, counters, t_end, tiles, toff, sperm, sinv, mark, rows, total;
+      status, counters, t_end, work, tiles, toff, sperm, sinv, mark, rows, total;
   int64_t S, part_items, n_tiles;
 };
 
@@ -81,6 +81,7 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
   L.status = take(c, 4);
   L.counters = take(c, 8 * 4);
   L.t_end = take(c, 8);
+  L.work = take(c, 4);
   L.tiles = take(c, 16 * kTileRecF4 * (size_t)n_tiles);
   L.toff = take(c, 4 * ((size_t)K + 1));
   L.sperm = take(c, 4 * (size_t)S);
@@ -259,6 +260,7 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, doub
   a.G = c->cfg.G;
   a.eps2 = c->cfg.eps * c->cfg.eps;
   a.status = c->d.status;
+  a.work_ctr = c->d.work_ctr;
   return a;
 }
 
@@ -425,7 +427,7 @@ void nb_default_config(nb_config* cfg) {
   cfg->bfactor = 0;
   cfg->graph_steps = 16;
   cfg->sort_sources = 1;
-  cfg->variant = 2;
+  cfg->variant = kMixDefaultVariant;
 }
 
 int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config* cfg, size_t* bytes) {
@@ -462,7 +464,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
 
   nb_ctx* c = new nb_ctx();
   c->cfg = *cfg;
-  if (c->cfg.precision == NB_DS || c->cfg.precision == NB_FP32) c->cfg.variant = 2;
+  if (c->cfg.precision == NB_DS || c->cfg.precision == NB_FP32) c->cfg.variant = kMixDefaultVariant;
   c->st = static_cast<cudaStream_t>(stream);
   c->off_host.assign(offsets, offsets + n_clusters + 1);
   c->mass_host.assign(mass, mass + N);
@@ -503,6 +505,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   d.status = reinterpret_cast<uint32_t*>(w + c->L.status);
   d.counters = reinterpret_cast<unsigned long long*>(w + c->L.counters);
   d.t_end = reinterpret_cast<int64_t*>(w + c->L.t_end);
+  d.work_ctr = reinterpret_cast<int32_t*>(w + c->L.work);
   d.tiles = reinterpret_cast<float4*>(w + c->L.tiles);
   d.toff = reinterpret_cast<int32_t*>(w + c->L.toff);
   d.n_tiles = n_tiles;

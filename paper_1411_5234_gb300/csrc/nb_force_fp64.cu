@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(NT) k_force_fp64(const ForceArgs a) {
   __shared__ __align__(128) dbl4 sv[2][JT];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int abort_flag;
+  __shared__ int32_t item_sh;
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -104,7 +105,10 @@ __global__ void __launch_bounds__(NT) k_force_fp64(const ForceArgs a) {
   const dbl4* __restrict__ gv = static_cast<const dbl4*>(a.src_b);
   const int32_t n_items = a.item_off[a.K];
 
-  for (int32_t w = blockIdx.x; w < n_items; w += gridDim.x) {
+  // dynamic item order when the plan provided a counter (see k_force_mixed)
+  const bool dyn = a.work_ctr != nullptr;
+  for (int32_t w = dyn ? grab_item(a.work_ctr, &item_sh) : (int32_t)blockIdx.x; w < n_items;
+       w = dyn ? grab_item(a.work_ctr, &item_sh) : w + (int32_t)gridDim.x) {
     const int32_t k = upper_bound_i32(a.item_off, a.K + 1, w) - 1;
     const int32_t B = a.bfac[k];
     const int32_t l = w - a.item_off[k];

@@ -2,33 +2,36 @@
 // kernel (the kernel itself is in nb_force_mixed.cuh).
 //
 // Shapes compiled in (selected per context by nb_config.variant; each
-// handles NT x IPT targets per work item):
-//   0: 128 threads x 2 targets, totals in registers, 1/s^2 = rsqrt^2
-//   1: 128 threads x 2 targets, totals in registers, 1/s^2 from the SFU
-//   2:  64 threads x 4 targets, totals in shared memory, 1/s^2 = rsqrt^2
-//   3: 256 threads x 1 target,  totals in registers, 1/s^2 from the SFU
-//   4:  64 threads x 3 targets, totals in shared memory, 1/s^2 = rsqrt^2
-//   5:  32 threads x 4 targets (one warp per CTA), shared-memory totals
+// handles NT x IPT targets per work item; all take work items in dynamic
+// order):
+//   0:  64 threads x 4 targets, shared-memory totals, two tiles per stage,
+//       near loop unrolled x4 (the default: 60.9 % of the FP32 peak at
+//       N = m = 2^20 on GB300, against 59.5-60.7 % for the next shapes)
+//   1:  as 0 with the near loop unrolled x8
+//   2:  64 x 4, one tile per stage, near loop unrolled x2
+//   3:  32 x 4 (one warp per CTA, 8 CTAs per SM), one tile per stage
+//   4:  64 x 3, two tiles per stage (10 warps per SM)
+//   5: 128 x 2, totals in registers, source loop unrolled x2, two tiles per stage
 // and, for nb_force calls that want no jerk, one acceleration-only shape.
 #include "../../include/nbody_gb300.h"
 #include "nb_force_mixed.cuh"
 
 namespace nb {
 namespace {
-template <bool POT> using S0 = mixk::MixShape<128, 2, POT, false, false, 2, 2>;
-template <bool POT> using S1 = mixk::MixShape<128, 2, POT, true, false, 2, 2>;
-template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 1, 4>;
-template <bool POT> using S3 = mixk::MixShape<256, 1, POT, true, false, 4, 2>;
-template <bool POT> using S4 = mixk::MixShape<64, 3, POT, false, true, 1, 5>;
-template <bool POT> using S5 = mixk::MixShape<32, 4, POT, false, true, 1, 8>;
+template <bool POT> using S0 = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepMixed, 4, 2>;
+template <bool POT> using S1 = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepMixed, 8, 2>;
+template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepMixed, 2, 1>;
+template <bool POT> using S3 = mixk::MixShape<32, 4, POT, false, true, 1, 8, true, mixk::kSepMixed, 4, 1>;
+template <bool POT> using S4 = mixk::MixShape<64, 3, POT, false, true, 1, 5, true, mixk::kSepMixed, 4, 2>;
+template <bool POT> using S5 = mixk::MixShape<128, 2, POT, false, false, 2, 2, true, mixk::kSepMixed, 4, 2>;
 // acceleration (and potential) only: 64 x 4 at 6 CTAs per SM was the fastest
 // of the 64x4 (5 or 6 CTAs/SM, unrolled or not), 128x2 and 256x1 shapes at
 // N = m = 2^20 (measured on GB300)
-template <bool POT> using SA = mixk::MixShape<64, 4, POT, false, true, 1, 6, false>;
-// the 64 x 4 shape with double-single separations everywhere, and with plain
+template <bool POT> using SA = mixk::MixShape<64, 4, POT, false, true, 1, 6, false, mixk::kSepMixed, 4, 2>;
+// the default shape with double-single separations everywhere, and with plain
 // FP32 separations (NB_DS, NB_FP32: accuracy and speed bounds of the mixed path)
-template <bool POT> using SD = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepDS>;
-template <bool POT> using SF = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepFP32>;
+template <bool POT> using SD = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepDS, 4, 2>;
+template <bool POT> using SF = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepFP32, 4, 2>;
 
 template <class Sh>
 cudaError_t launch_shape(const ForceArgs& a, int grid, cudaStream_t st) {

@@ -27,19 +27,24 @@
 // Everything after the separation is FP32 (hardware rsqrt and reciprocal);
 // the jerk term is formed per pair as m (w + t d) / s^3 with t = -3 d.w / s^2
 // (its rounding is relative to |w| + 3 |d.w| |d| / s^2, the magnitude of the
-// two terms taken apart); sums are accumulated per tile in FP32 and folded
-// into a compensated (hi, lo) FP32 pair per tile (two-sum), then combined in
-// FP64.
+// two terms taken apart); sums are accumulated per pipeline stage in FP32
+// and folded into a compensated (hi, lo) FP32 pair per stage (two-sum), then
+// combined in FP64.
 //
 // GB300 mapping:
-//   * persistent CTAs loop over work items (cluster, i-tile, j-chunk); the
-//     j-chunk split is the i-splitting of Sec. 2 item 3 (Bfactor): B chunks
-//     of the source range per i-tile, partial sums reduced afterwards in a
-//     fixed order;
-//   * source tiles and their (centre, radius) record are staged in shared
-//     memory (Sec. 2 item 5) by bulk copies (TMA engine, cp.async.bulk) into a
-//     two-stage ring guarded by mbarriers; waits are bounded and report
-//     NB_ETIMEOUT instead of hanging;
+//   * persistent CTAs take work items (cluster, i-tile, j-chunk) from a
+//     device counter that the plan zeroes before every launch; the j-chunk
+//     split is the i-splitting of Sec. 2 item 3 (Bfactor): B chunks of the
+//     source range per i-tile, partial sums reduced afterwards in a fixed
+//     order.  Items are handed out dynamically because the warp scheduler
+//     favours older warps: with a fixed share per CTA the younger CTAs of an
+//     SM finish late and run alone on their sub-partition, where one warp
+//     cannot keep the FMA pipe busy (measured: 1 ms spread of finish times in
+//     a 2.4 ms launch of identical shares);
+//   * source tiles and their cell records (centre, radius) are staged in
+//     shared memory (Sec. 2 item 5) by bulk copies (TMA engine,
+//     cp.async.bulk), ST tiles per stage, into a two-stage ring guarded by
+//     mbarriers; waits are bounded and report NB_ETIMEOUT instead of hanging;
 //   * every pair operation is a packed f32x2 instruction over two sources,
 //     feeding the FP32 pipe at full width; IPT targets per thread share each
 //     shared-memory load.
@@ -50,7 +55,12 @@
 // totals in shared memory instead of registers, UNR unrolls the source loop,
 // MINB is the CTAs-per-SM hint of __launch_bounds__, JERK false computes the
 // acceleration (and potential) alone: no velocities, 12 f32x2 instructions
-// per two interactions instead of 26 (for acceleration-only integrators).
+// per two interactions instead of 26 (for acceleration-only integrators),
+// SEP the separation mode, NU unrolls the near-cell loop (it runs one target
+// at a time, so its groups are independent chains worth interleaving), ST
+// tiles of kMixJT sources per pipeline stage: the per-tile FP32 sums are
+// folded into the compensated totals once per stage, so ST = 2 halves the
+// flushes, syncs and waits (FP32 runs of 128 terms per lane instead of 64).
 #pragma once
 #include "nb_internal.cuh"
 
@@ -75,11 +85,11 @@ enum { cDXH = 0, cDYH, cDZH, cM, cVX, cVY, cVZ, cDXL, cDYL, cDZL };
 enum { kSepMixed = 0, kSepDS = 1, kSepFP32 = 2 };
 
 template <int NT_, int IPT_, bool POT_, bool RCP_, bool SMT_, int UNR_, int MINB_,
-          bool JERK_ = true, int SEP_ = kSepMixed>
+          bool JERK_ = true, int SEP_ = kSepMixed, int NU_ = 1, int ST_ = 1>
 struct MixShape {
   static constexpr int NT = NT_, IPT = IPT_, NI = NT_ * IPT_, UNR = UNR_, MINB = MINB_;
   static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_, JERK = JERK_;
-  static constexpr int SEP = SEP_;
+  static constexpr int SEP = SEP_, NU = NU_, ST = ST_;
   static_assert(NT_ * IPT_ <= kMixNI, "partial-sum rows hold at most kMixNI targets");
 };
 
@@ -121,6 +131,17 @@ __device__ __forceinline__ void ds_sub(float ah, float al, float bh, float bl, f
   const float bb = s - ah;
   float err = (ah - (s - bb)) + (-bh - bb);
   err += al - bl;
+  rh = s + err;
+  rl = err - (rh - s);
+}
+
+// c - (bh + bl) in double-single for an FP32 value c (a cell centre, whose
+// double-single low part is zero).
+__device__ __forceinline__ void ds_sub0(float c, float bh, float bl, float& rh, float& rl) {
+  const float s = c - bh;
+  const float bb = s - c;
+  float err = (c - (s - bb)) + (-bh - bb);
+  err -= bl;
   rh = s + err;
   rl = err - (rh - s);
 }
@@ -192,7 +213,7 @@ template <class Sh, bool MASK>
 __device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile, int ngroups,
                                               int64_t slot0, Target& s, f2 elx, f2 ely, f2 elz,
                                               int64_t slot, f2 eps2) {
-#pragma unroll 1
+#pragma unroll Sh::NU
   for (int g = 0; g < ngroups; ++g) {
     const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
@@ -301,13 +322,13 @@ __device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT>& T, flo
   if (Sh::POT) T.add(col, 6, lanes_sum(s.pt));
 }
 
-// Tile t0 .. t0 + cnt of the source slots (cnt a multiple of 4) plus its
-// cell records (centre, radius).
+// Slots t0 .. t0 + cnt (cnt a multiple of 4, at most a stage) plus the cell
+// records (centre, radius) of the tiles they span; t0 starts a tile.
 __device__ __forceinline__ void issue_tile(float4* stage, float4* rec, uint64_t* bar,
                                            const float4* src, const float4* tiles,
                                            int64_t t0, int64_t cnt, int64_t tile_idx) {
   const uint32_t bytes = static_cast<uint32_t>(cnt / 4) * kGroupBytes;
-  constexpr uint32_t rec_bytes = 16u * kTileRecF4;
+  const uint32_t rec_bytes = 16u * kTileRecF4 * static_cast<uint32_t>(ceil_div64(cnt, JT));
   mbar_arrive_expect(bar, bytes + rec_bytes);
   bulk_g2s(stage, src + (t0 >> 2) * kGroupF4, bytes, bar);
   bulk_g2s(rec, tiles + kTileRecF4 * tile_idx, rec_bytes, bar);
@@ -316,10 +337,12 @@ __device__ __forceinline__ void issue_tile(float4* stage, float4* rec, uint64_t*
 template <class Sh>
 __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArgs a) {
   constexpr int NT = Sh::NT, IPT = Sh::IPT, NI = Sh::NI;
-  __shared__ __align__(128) float4 stage[2][kTileF4];
-  __shared__ __align__(16) float4 rec[2][kTileRecF4];
+  constexpr int SJ = Sh::ST * JT;  // sources per pipeline stage
+  __shared__ __align__(128) float4 stage[2][Sh::ST * kTileF4];
+  __shared__ __align__(16) float4 rec[2][Sh::ST * kTileRecF4];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int abort_flag;
+  __shared__ int32_t item_sh;
   __shared__ float tot_sh[Sh::SMT ? IPT * 2 * kTotComps * NT : 1];
   __shared__ TargetPosSh<IPT, NT> tpos;
   const int tid = threadIdx.x;
@@ -338,7 +361,10 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
   const f2 eps2 = f2_pack(e2, e2);
   const int32_t n_items = a.item_off[a.K];
 
-  for (int32_t w = blockIdx.x; w < n_items; w += gridDim.x) {
+  // dynamic item order when the plan provided a counter, else a fixed share
+  const bool dyn = a.work_ctr != nullptr;
+  for (int32_t w = dyn ? grab_item(a.work_ctr, &item_sh) : (int32_t)blockIdx.x; w < n_items;
+       w = dyn ? grab_item(a.work_ctr, &item_sh) : w + (int32_t)gridDim.x) {
     const int32_t k = upper_bound_i32(a.item_off, a.K + 1, w) - 1;
     const int32_t B = a.bfac[k];
     const int32_t l = w - a.item_off[k];
@@ -405,22 +431,23 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       tot[r].zero(tot_sh + r * 2 * kTotComps * NT + tid);
     }
 
-    const int64_t ntile = ceil_div64(j1 - j0, JT);
-    uint32_t n_near = 0;  // tiles this warp took on the near path
+    // pipeline stages of SJ slots (the chunk starts on a tile boundary)
+    const int64_t ntile = ceil_div64(j1 - j0, SJ);
+    uint32_t n_near = 0;  // cells this warp took on the near path
     if (tid == 0) {
-      issue_tile(stage[0], rec[0], &bar[0], src, tiles, j0, min((int64_t)JT, j1 - j0),
+      issue_tile(stage[0], rec[0], &bar[0], src, tiles, j0, min((int64_t)SJ, j1 - j0),
                  tk0 + (j0 - sk0) / JT);
       pending[0] = true;
       if (ntile > 1) {
-        issue_tile(stage[1], rec[1], &bar[1], src, tiles, j0 + JT,
-                   min((int64_t)JT, j1 - j0 - JT), tk0 + (j0 - sk0) / JT + 1);
+        issue_tile(stage[1], rec[1], &bar[1], src, tiles, j0 + SJ,
+                   min((int64_t)SJ, j1 - j0 - SJ), tk0 + (j0 - sk0) / JT + Sh::ST);
         pending[1] = true;
       }
     }
     for (int64_t t = 0; t < ntile; ++t) {
       const int st = static_cast<int>(t & 1);
-      const int64_t t0 = j0 + t * JT;
-      const int64_t cnt = min((int64_t)JT, j1 - t0);
+      const int64_t t0 = j0 + t * SJ;
+      const int64_t cnt = min((int64_t)SJ, j1 - t0);
       const bool ok_me = mbar_wait(&bar[st], used[st] & 1u, kWaitBudget);
       used[st] += 1;
       if (tid == 0) pending[st] = false;
@@ -433,20 +460,21 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       const bool ok = __syncthreads_and(ok_me) != 0;
       const int ng = ok ? static_cast<int>(cnt >> 2) : 0;
 #pragma unroll 1
-      for (int q = 0; q < kMixCells; ++q) {
+      for (int q = 0; q < Sh::ST * kMixCells; ++q) {
         const int g0 = q * kCellGroups;
         const int ngq = min(ng - g0, kCellGroups);
         if (ngq <= 0) break;  // uniform: ng is the same in every thread
-        const float4 ch = rec[st][2 * q], cl = rec[st][2 * q + 1];
+        // the centre is an FP32 point (its double-single low part is zero)
+        const float4 ch = rec[st][2 * q];
         const float far_lim = kFarRatio2 * ch.w * ch.w;
         bool far = true;
 #pragma unroll
         for (int r = 0; r < IPT; ++r) {
           const TargetPos tp = load_tpos(tpos, r, tid);
           float exh, exl, eyh, eyl, ezh, ezl;
-          ds_sub(ch.x, cl.x, tp.xh, tp.xl, exh, exl);
-          ds_sub(ch.y, cl.y, tp.yh, tp.yl, eyh, eyl);
-          ds_sub(ch.z, cl.z, tp.zh, tp.zl, ezh, ezl);
+          ds_sub0(ch.x, tp.xh, tp.xl, exh, exl);
+          ds_sub0(ch.y, tp.yh, tp.yl, eyh, eyl);
+          ds_sub0(ch.z, tp.zh, tp.zl, ezh, ezl);
           tg[r].ex = bcast(exh);
           tg[r].ey = bcast(eyh);
           tg[r].ez = bcast(ezh);
@@ -480,9 +508,9 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
           for (int r = 0; r < IPT; ++r) {
             const TargetPos tp = load_tpos(tpos, r, tid);
             float h, lx, ly, lz;
-            ds_sub(ch.x, cl.x, tp.xh, tp.xl, h, lx);
-            ds_sub(ch.y, cl.y, tp.yh, tp.yl, h, ly);
-            ds_sub(ch.z, cl.z, tp.zh, tp.zl, h, lz);
+            ds_sub0(ch.x, tp.xh, tp.xl, h, lx);
+            ds_sub0(ch.y, tp.yh, tp.yl, h, ly);
+            ds_sub0(ch.z, tp.zh, tp.zl, h, lz);
             // the slot test excludes j == i where the target's own cell is near
             tile_near_one<Sh, true>(cell, ngq, c0, tg[r], bcast(lx), bcast(ly), bcast(lz),
                                     tp.slot, eps2);
@@ -496,8 +524,8 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       __syncthreads();
       if (abort_flag) goto drain;
       if (tid == 0 && t + 2 < ntile) {
-        issue_tile(stage[st], rec[st], &bar[st], src, tiles, t0 + 2 * JT,
-                   min((int64_t)JT, j1 - t0 - 2 * JT), tk0 + (t0 - sk0) / JT + 2);
+        issue_tile(stage[st], rec[st], &bar[st], src, tiles, t0 + 2 * SJ,
+                   min((int64_t)SJ, j1 - t0 - 2 * SJ), tk0 + (t0 - sk0) / JT + 2 * Sh::ST);
         pending[st] = true;
       }
     }

@@ -217,6 +217,8 @@ __device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p, bool 
   __shared__ int32_t shi[32];
   __shared__ int32_t bg_sh;
   const int32_t K = d.K;
+  // the force kernel's dynamic item counter starts from zero every launch
+  if (threadIdx.x == 0 && d.work_ctr) *d.work_ctr = 0;
   unsigned long long nit = 0, inter = 0;
   for (int32_t k = threadIdx.x; k < K; k += blockDim.x) {
     const int64_t mk = d.act_off[k + 1] - d.act_off[k];
@@ -248,6 +250,10 @@ __device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p, bool 
           const float e = __fdiv_rn((float)n * (float)b, (float)rounds * (float)g);
           if (e > best + 1e-3f) { best = e; bg = b; }
         }
+        // at least kItemsPerCta items per CTA, so that the dynamic item order
+        // can even out CTAs that run at different speeds
+        const uint32_t bmin = (kItemsPerCta * g + n - 1) / n;
+        if (bg < (int64_t)bmin) bg = bmin;
       }
       const int64_t cap = max((int64_t)1, p.part_items / (int64_t)nit);
       if (bg > cap) bg = cap;

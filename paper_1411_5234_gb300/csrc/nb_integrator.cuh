@@ -10,6 +10,9 @@ namespace nb {
 // (k_reduce); larger ones, in the same kernel, in segments of kWideRows partial
 // rows (one per warp of its CTA).
 constexpr int kReduceSerial = 16;
+// The plan splits the sources so that a force launch has at least this many
+// work items per persistent CTA (taken in dynamic order).
+constexpr uint32_t kItemsPerCta = 4;
 constexpr int kWideRows = 32;
 
 // Entries of k_reduce's arrival counters (large splits) for a partial-sum buffer of

@@ -37,6 +37,7 @@ constexpr int kMixNI = kMixNT * kMixIPT;
 constexpr int kMixJT = 128;          // sources per shared-memory tile (multiple of 4)
 constexpr int kMixJD = 64;           // sources per cell (one centre/radius record)
 constexpr int kMixCells = kMixJT / kMixJD;  // cells per tile
+constexpr int kMixDefaultVariant = 0;       // mixed kernel shape of nb_default_config
 constexpr int kTileRecF4 = 2 * kMixCells;   // float4 of cell records per tile
 // FP64 force kernel shape.
 constexpr int kF64NT = 128;
@@ -81,6 +82,7 @@ struct Dev {
   unsigned long long* counters = nullptr;  // [0] interactions [1] block steps
                                            // [2] warp-tiles [3] near warp-tiles
   int64_t* t_end = nullptr;      // 1
+  int32_t* work_ctr = nullptr;   // next work item of the force kernels (zeroed by the plan)
 };
 
 // Targets, sources and outputs of one force launch.
@@ -108,6 +110,7 @@ struct ForceArgs {
   double G;
   double eps2;
   uint32_t* status;
+  int32_t* work_ctr;        // next work item (zeroed by the plan; nullptr: a fixed share per CTA)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -240,6 +243,16 @@ __device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T x) {
   T err = (hi - (s - bp)) + (x - bp);
   hi = s;
   lo += err;
+}
+
+// Next work item of a persistent force kernel from the device counter
+// (every thread of the CTA calls it; one atomic per item, broadcast through
+// shared memory).
+__device__ __forceinline__ int32_t grab_item(int32_t* ctr, int32_t* sh) {
+  __syncthreads();  // every thread has read the previous value
+  if (threadIdx.x == 0) *sh = atomicAdd(ctr, 1);
+  __syncthreads();
+  return *sh;
 }
 
 __device__ __forceinline__ int32_t upper_bound_i32(const int32_t* a, int32_t n, int32_t v) {

@@ -49,6 +49,8 @@ constexpr size_t kTileBytes = align_up(16 * kTileRecF4 * (size_t)kNoAllocTiles);
 constexpr size_t kOffSmall = kOffTiles + kTileBytes;
 constexpr size_t kSmallBytes = 4096;  // offsets, plan words, status, counters
 constexpr size_t kNoAllocBytes = kOffSmall + kSmallBytes;  // 6,705,664 bytes
+// the status word of the last call (read back by nb_noalloc_status)
+constexpr size_t kOffStatus = kOffSmall + 256 + 12 * sizeof(int32_t);
 static_assert(kNoAllocBytes == 6705664, "documented size of the fixed array");
 
 static_assert(64 + wide_counter_entries(kNoAllocItems) <= (kSmallBytes - 256) / 4,
@@ -66,10 +68,13 @@ struct DeviceSetup {
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-// Single-cluster offsets, the identity source order and the zeroed status.
+// Single-cluster offsets, the identity source order, the zeroed status and
+// the zeroed arrival counters of the wide-split reduction (a call whose
+// reduction did not finish must not leave them behind for the next one).
 __global__ void k_noalloc_setup(int64_t n, int64_t n_pad, int64_t m, int32_t n_tiles,
                                 int64_t* off, int64_t* soff, int32_t* act_off, int32_t* toff,
-                                uint32_t* status) {
+                                uint32_t* status, int32_t* wide_cnt, int64_t n_wide) {
+  for (int64_t i = threadIdx.x; i < n_wide; i += blockDim.x) wide_cnt[i] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     off[0] = 0;
     off[1] = n;
@@ -177,7 +182,7 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   d.act_off = small32;       // 2 entries
   d.item_off = small32 + 4;  // 2 entries
   d.bfac = small32 + 8;      // 1 entry
-  d.status = reinterpret_cast<uint32_t*>(small32 + 12);
+  d.status = reinterpret_cast<uint32_t*>(base + kOffStatus);  // small32 + 12
   d.src_mix = reinterpret_cast<float4*>(base + kOffSources);
   d.src64_pos = reinterpret_cast<dbl4*>(base + kOffSources);
   d.src64_vel = reinterpret_cast<dbl4*>(base + kOffSources + 32 * kNoAllocSlots);
@@ -186,11 +191,12 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   d.tiles = reinterpret_cast<float4*>(base + kOffTiles);
   d.toff = small32 + 16;     // 2 entries
   d.wt_off = small32 + 20;   // 2 entries
-  d.wide_cnt = small32 + 64; // wide_counter_entries(kNoAllocItems), zero from load time
+  d.work_ctr = small32 + 24; // the force kernel's dynamic item counter (zeroed by the plan)
+  d.wide_cnt = small32 + 64; // wide_counter_entries(kNoAllocItems), zeroed by the set-up
   const int32_t n_tiles = static_cast<int32_t>((n_pad + kMixJT - 1) / kMixJT);
 
-  k_noalloc_setup<<<1, 32, 0, st>>>(n, n_pad, m, n_tiles, d.off, d.soff, d.act_off, d.toff,
-                                    d.status);
+  k_noalloc_setup<<<1, 256, 0, st>>>(n, n_pad, m, n_tiles, d.off, d.soff, d.act_off, d.toff,
+                                     d.status, d.wide_cnt, wide_counter_entries(kNoAllocItems));
   if (f64)
     k_noalloc_pack64<<<static_cast<int>((n_pad + 255) / 256), 256, 0, st>>>(
         pos, vel, mass, n, n_pad, d.src64_pos, d.src64_vel);
@@ -199,9 +205,9 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
                                                    d.tiles);
   if (cudaGetLastError() != cudaSuccess) return NB_ECUDA;
 
-  const int grid = ds->sms * (f64 ? force_fp64_ctas_per_sm() : force_mixed_ctas_per_sm(2));
+  const int grid = ds->sms * (f64 ? force_fp64_ctas_per_sm() : force_mixed_ctas_per_sm(kMixDefaultVariant));
   PlanArgs p{};
-  p.NI = f64 ? kF64NI : force_mixed_ni(2);
+  p.NI = f64 ? kF64NI : force_mixed_ni(kMixDefaultVariant);
   p.JT = f64 ? kF64JT : kMixJT;
   p.grid = grid;
   p.forced_b = 0;
@@ -237,10 +243,26 @@ extern "C" int nb_force_noalloc(const double* pos, const double* vel, const doub
   a.G = G;
   a.eps2 = eps * eps;
   a.status = d.status;
+  a.work_ctr = d.work_ctr;
   cudaError_t e = f64 ? launch_force_fp64(a, grid, kF64Full, st)
-                      : launch_force_mixed(a, grid, pot != nullptr, 2, st);
+                      : launch_force_mixed(a, grid, pot != nullptr, kMixDefaultVariant, st);
   if (e != cudaSuccess) return NB_ECUDA;
   if (launch_reduce(a, p.NI, true, m, ds->sms, st) != cudaSuccess) return NB_ECUDA;
   return NB_OK;
 }
 
+extern "C" int nb_noalloc_status(void* stream) {
+  DeviceSetup* ds = nullptr;
+  const int rc = setup_device(&ds);
+  if (rc != NB_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t s = 0;
+  const void* word = ds->base + kOffStatus;
+  if (cudaMemcpyAsync(&s, word, sizeof s, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return NB_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return NB_ECUDA;
+  if (s & kStatusTimeout) return NB_ETIMEOUT;
+  if (s & kStatusNonFinite) return NB_ENONFINITE;
+  if (s & kStatusInval) return NB_EINVAL;
+  return NB_OK;
+}

@@ -19,6 +19,7 @@ from . import build as _build
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ETIMEOUT, NB_ENONFINITE, NB_ESTATE = range(7)
 NB_FP64, NB_MIXED, NB_DS, NB_FP32 = 0, 1, 2, 3
 MIXED_VARIANTS = 6    # NB_MIXED_VARIANTS: shapes of the mixed force kernel
+DEFAULT_VARIANT = 0   # the shape nb_default_config selects
 
 FUNCTIONS = [
     "nb_default_config", "nb_workspace_size", "nb_init", "nb_free", "nb_predict", "nb_force",
@@ -26,6 +27,7 @@ FUNCTIONS = [
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
     "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
     "nb_energies", "nb_autotune", "nb_step_leapfrog", "nb_check_wait_timeout",
+    "nb_noalloc_status",
 ]
 
 
@@ -81,6 +83,7 @@ def _load() -> ctypes.CDLL:
         "nb_autotune": (ctypes.c_int, [P, P, P]),
         "nb_force_noalloc": (ctypes.c_int, [P, P, P, i64, P, i64, ctypes.c_double,
                                             ctypes.c_double, i32, P, P, P, P]),
+        "nb_noalloc_status": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -363,3 +366,9 @@ def force_noalloc(pos, vel, mass, targets, G=1.0, eps=1e-4, precision=NB_MIXED,
            "nb_force_noalloc")
     return acc, jerk, pot
 
+
+def noalloc_status(stream=None) -> int:
+    """nb_noalloc_status: the device status (NB_OK or an NB_E* code) of the
+    last force_noalloc call on ``stream`` (synchronises it)."""
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return int(lib.nb_noalloc_status(ctypes.c_void_p(st.cuda_stream)))
