@@ -14,7 +14,8 @@ Reported (one JSON line from rank 0):
   e2e        the same through the C ABI with pinned HOST buffers: state copied
              in, one block step, state copied out, every step;
   roofline   the mixed force kernel at 38 flops per interaction against the
-             FP32 peak 152 SMs x 128 lanes x 2 flops x 2.070 GHz;
+             FP32 peak (SM count read at run time) x 128 lanes x 2 flops x 2.070
+             GHz, and the measured f32x2 FMA rate (nb_measure_rate);
   sweep      nb_force alone at active fractions 2^-10 .. 1 (mixed) and
              2^-10 .. 2^-6 (FP64), with the mixed path's error vs the FP64
              path (the oracle checks both paths in tests/);
@@ -43,7 +44,22 @@ sys.path.insert(0, ROOT)
 
 FLOPS_PER_INTERACTION = 38          # acceleration + jerk convention
 FLOPS_PER_INTERACTION_ACC = 20      # acceleration-only convention
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0
+_SMS = []
+
+
+def sm_count():
+    """SMs of the GPU in use (read once at run time; GB300: 152)."""
+    if not _SMS:
+        import torch
+        _SMS.append(torch.cuda.get_device_properties(torch.cuda.current_device())
+                    .multi_processor_count)
+    return _SMS[0]
+
+
+def fp32_peak_flops(mhz=SM_MAX_MHZ):
+    """Nominal FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return sm_count() * FP32_LANES * 2 * mhz * 1e6
 METRIC = "pair-interactions/s (and % FP32 peak) at N=2^20, mixed vs FP64, at stated error"
 KERNEL_FILES = [os.path.join(ROOT, "paper_1411_5234_gb300", "csrc", f)
                 for f in ("nb_force_mixed.cuh", "nb_force_mixed.cu", "nb_internal.cuh")]
@@ -226,7 +242,7 @@ def workload_leapfrog(args):
     rate = args.steps * n * n / (total_ms * 1e-3)
     per = force_ms * 1e-3 / max(launches, 1)
     achieved = FLOPS_PER_INTERACTION_ACC * n * n / per / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = fp32_peak_flops() / 1e12
     print(json.dumps({
         "workload": f"leapfrog (kick-drift-kick, shared step 2^-{L}): Plummer N={n} Kroupa, "
                     "eps=1e-4, mixed, acceleration-only force",
@@ -275,7 +291,7 @@ def kernel_case(args):
                       "ms_per_launch": per, "interactions_per_s": rate,
                       "flops_per_interaction": flops,
                       "frac_fp32_peak": flops * rate
-                      / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6)}), flush=True)
+                      / fp32_peak_flops()}), flush=True)
     sim.close()
     return 0
 
@@ -531,19 +547,31 @@ def main():
     clocks = clk.summary()
     force_avg_s = force_ms * 1e-3 / max(force_launches, 1)
     achieved = FLOPS_PER_INTERACTION * inter_step / force_avg_s / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = fp32_peak_flops() / 1e12
     traffic = traffic_from_profile(KERNEL_FILES)
     roofline = {"bound": "alu", "kernel": "k_force_mixed", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "flops_per_interaction": FLOPS_PER_INTERACTION,
-                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz (max clock)",
+                "peak_basis": f"FP32 FMA: {sm_count()} SMs (read at run time) x 128 lanes x 2 "
+                              f"flops x 2070 MHz (max clock)",
                 "force_ms_per_launch": force_avg_s * 1e3,
                 "force_share_of_step": force_ms / max(total_ms, 1e-9) if world == 1 else None}
     if clocks.get("sm_mhz"):
-        pk = SMS * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12
+        pk = fp32_peak_flops(clocks["sm_mhz"]) / 1e12
         roofline["peak_at_sampled_clock"] = pk
         roofline["frac_at_sampled_clock"] = achieved / pk
 
+    # measured FMA rates of this GPU (nb_measure_rate: SM-clock cycles, so
+    # independent of the clock it ran at) beside the nominal 128 lanes/SM/clk
+    r2 = sim.measure_rate(0)
+    r64 = sim.measure_rate(2)
+    mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    pk_meas = sm_count() * r2 * 2 * mhz * 1e6 / 1e12
+    roofline["measured_rates"] = {
+        "ffma2_lanes_per_sm_clk": r2, "dfma_lanes_per_sm_clk": r64,
+        "peak_measured_ffma2": pk_meas, "frac_of_measured_ffma2": achieved / pk_meas,
+        "basis": f"measured f32x2 FMA lanes/SM/clk x {sm_count()} SMs x 2 flops x {mhz:.0f} MHz "
+                 "(sampled clock)"}
     roofline["kernel_shape_variant"] = sim.cfg.variant
     if tune:
         roofline["autotune"] = tune
@@ -622,7 +650,7 @@ def sweep(nbody, inputs, torch, cl):
                      "ms": best}
             if name == "mixed":
                 entry["frac_fp32_peak"] = (FLOPS_PER_INTERACTION * rate
-                                           / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6))
+                                           / fp32_peak_flops())
             out[name].append(entry)
     # acceleration only (nb_force with jerk == NULL), 20 flops per interaction
     out["mixed_acc_only"] = []
@@ -644,7 +672,7 @@ def sweep(nbody, inputs, torch, cl):
             "active_fraction": f"2^-{k}", "m": m, "interactions_per_s": rate, "ms": best,
             "flops_per_interaction": FLOPS_PER_INTERACTION_ACC,
             "frac_fp32_peak": (FLOPS_PER_INTERACTION_ACC * rate
-                               / (SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6))})
+                               / fp32_peak_flops())})
     # the mixed path's separation-mode bounds (NB_DS, NB_FP32) at m = 2^14
     idx = inputs.random_active(n, 4096, seed=123)
     act = torch.as_tensor(idx, device="cuda")

@@ -166,8 +166,14 @@ int nb_correct(nb_ctx *ctx, int64_t t_ticks, const int32_t *active_idx,
  * t_next, evaluates the force on its active set {i : t_i + dt_i = t_next}
  * and corrects that set.  All sizes live on the device, so the sequence is
  * launched without host synchronisation (CUDA graphs of graph_steps steps).
- * Asynchronous. */
-int nb_step_block(nb_ctx *ctx, int64_t n_steps);
+ * Asynchronous when both outputs are NULL.  Otherwise the call waits for the
+ * steps and reports (host outputs): t_ticks_out, the smallest cluster block
+ * time after the last step (the common time of a single cluster);
+ * m_last_out, the number of particles corrected in the last step, summed over
+ * the clusters that stepped (0 when n_steps == 0 or every cluster had
+ * reached its end time). */
+int nb_step_block(nb_ctx *ctx, int64_t n_steps, int64_t *t_ticks_out,
+                  int64_t *m_last_out);
 
 /* Clusters stop stepping once their time reaches t_end_ticks (a multiple of
  * 2^-level_min time units keeps every particle synchronised there).
@@ -189,24 +195,31 @@ int nb_step_leapfrog(nb_ctx *ctx, int64_t n_steps, int64_t dt_ticks);
 
 /* FP64 kinetic and softened potential energy of cluster `cluster` (-1: all
  * clusters summed), with every particle predicted to its cluster's current
- * block time.  Host outputs; synchronises. */
+ * block time: E_kin = 1/2 sum_i m_i |v_i|^2 and E_pot = 1/2 sum_i m_i pot_i,
+ * pot_i = -G sum_{j != i} m_j / (|r_ij|^2 + eps^2)^(1/2), the potential whose
+ * gradient is the softened force of Eq. 2 (Sec. 1: the softening enters the
+ * gravitational potential).  Host outputs; synchronises. */
 int nb_energy(nb_ctx *ctx, int32_t cluster, double *ekin, double *epot);
 
-/* The same energies for every cluster from ONE potential evaluation of the
- * whole context: ekin[k], epot[k] for k < n_clusters (host arrays).
- * Synchronises. */
+/* The same energies (as nb_energy, the softened potential of Eq. 2) for
+ * every cluster from ONE potential evaluation of the whole context: ekin[k],
+ * epot[k] for k < n_clusters (host arrays).  Synchronises. */
 int nb_energies(nb_ctx *ctx, double *ekin, double *epot);
 
 /* Copy the state to host arrays (any pointer may be NULL): pos, vel, acc,
- * jerk (n x 3), t (n ticks), level (n).  The vectors are packed on the device
- * and copied straight into the caller's arrays (pinned arrays copy at full
- * host-link bandwidth).  Synchronises. */
+ * jerk (n x 3), t (n ticks), level (n) -- the particle state of Eq. 1
+ * (positions, velocities, masses) plus the Hermite scheme's derivatives and
+ * the block-step bookkeeping of Sec. 2 items 1 and 2.  The vectors are packed
+ * on the device and copied straight into the caller's arrays (pinned arrays
+ * copy at full host-link bandwidth).  Synchronises. */
 int nb_get_state(nb_ctx *ctx, double *pos, double *vel, double *acc,
                  double *jerk, int64_t *t, int32_t *level);
 
-/* Overwrite the state from host arrays (all six required; masses keep their
+/* Overwrite the state (as nb_get_state describes it, Eq. 1 and Sec. 2
+ * items 1 and 2) from host arrays (all six required; masses keep their
  * nb_init values).  Levels must lie in [level_min, level_max] and each time
- * must be a multiple of its step.  Synchronises. */
+ * must be a multiple of its step (Sec. 2 item 2: power-of-two steps).
+ * Synchronises. */
 int nb_set_state(nb_ctx *ctx, const double *pos, const double *vel,
                  const double *acc, const double *jerk, const int64_t *t,
                  const int32_t *level);
@@ -247,6 +260,17 @@ int nb_tile_stats(nb_ctx *ctx, int64_t *warp_tiles, int64_t *near_warp_tiles);
 #define NB_TUNE_POINTS 3
 #define NB_MIXED_VARIANTS 6
 int nb_autotune(nb_ctx *ctx, int32_t *variant_out, double *ms_out);
+
+/* Arithmetic-rate probe for the roofline of the force kernels (the paper has
+ * no counterpart): runs independent FMA chains in 4 CTAs of 256 threads per
+ * SM and returns the FMA lanes per SM per SM-clock cycle (lanes_per_sm_clock,
+ * host; the median over SMs, counted with the SM cycle counter, so it does
+ * not depend on the clock the GPU ran at).  kind 0: packed f32x2 FMA (two
+ * lanes per instruction, the mixed kernel's arithmetic), 1: FP32 FMA, 2: FP64
+ * FMA.  Nominal: 128 FP32 lanes per SM per clock.  Uses the workspace's
+ * partial-sum buffer as scratch (call it between force evaluations).
+ * Synchronises. */
+int nb_measure_rate(nb_ctx *ctx, int32_t kind, double *lanes_per_sm_clock);
 
 /* Sticky device status (NB_OK or an NB_E* code); synchronises. */
 int nb_status(nb_ctx *ctx);

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnbody_gb300.so")
 SOURCES = ["nb_force_mixed.cu", "nb_force_fp64.cu", "nb_integrator.cu", "nb_api.cu",
-           "nb_noalloc.cu"]
+           "nb_noalloc.cu", "nb_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "-Wno-deprecated-gpu-targets"]

@@ -680,9 +680,13 @@ int nb_step_leapfrog(nb_ctx* c, int64_t n_steps, int64_t dt_ticks) {
   return NB_OK;
 }
 
-int nb_step_block(nb_ctx* c, int64_t n_steps) {
+int nb_step_block(nb_ctx* c, int64_t n_steps, int64_t* t_ticks_out, int64_t* m_last_out) {
   NvtxRange nvtx_range("nb_step_block");
   if (!c || n_steps < 0) return NB_EINVAL;
+  if (n_steps == 0 && m_last_out) {
+    // nothing corrected: clear the count the report below reads
+    NB_TRY(cudaMemsetAsync(c->d.act_off + c->d.K, 0, sizeof(int32_t), c->st));
+  }
   const int G = c->cfg.graph_steps;
   const bool graphs = G > 0 && c->st != nullptr && !c->graph_broken && !c->prof;
   if (graphs && c->graph == nullptr && n_steps >= G) {
@@ -710,6 +714,19 @@ int nb_step_block(nb_ctx* c, int64_t n_steps) {
     }
   }
   for (; left > 0; --left) NB_TRY(enqueue_block_step(c));
+  if (!t_ticks_out && !m_last_out) return NB_OK;
+  // report: the last step's active count (act_off[K], which its plan wrote)
+  // and the clusters' block times
+  int32_t m_last = 0;
+  std::vector<int64_t> tc(c->d.K);
+  NB_TRY(cudaMemcpyAsync(&m_last, c->d.act_off + c->d.K, sizeof m_last, cudaMemcpyDeviceToHost,
+                         c->st));
+  NB_TRY(cudaMemcpyAsync(tc.data(), c->d.t_cur, 8 * (size_t)c->d.K, cudaMemcpyDeviceToHost,
+                         c->st));
+  const int rc = sync_status(c);
+  if (rc != NB_OK) return rc;
+  if (t_ticks_out) *t_ticks_out = *std::min_element(tc.begin(), tc.end());
+  if (m_last_out) *m_last_out = m_last;
   return NB_OK;
 }
 
@@ -963,6 +980,50 @@ int nb_autotune(nb_ctx* c, int32_t* variant_out, double* ms_out) {
 int nb_status(nb_ctx* c) {
   if (!c) return NB_EINVAL;
   return sync_status(c);
+}
+
+int nb_measure_rate(nb_ctx* c, int32_t kind, double* lanes_per_sm_clock) {
+  NvtxRange nvtx_range("nb_measure_rate");
+  if (!c || kind < 0 || kind > 2 || !lanes_per_sm_clock) return NB_EINVAL;
+  const int per_sm = 4;
+  const int ctas = c->sms * per_sm;
+  const int iters = kind == 2 ? 2000 : 100000;
+  // the partial-sum buffer is scratch between force evaluations
+  const size_t need = probe_scratch_bytes(ctas);
+  if (need > c->L.part_items * kPartialComps * (size_t)kMixNI * sizeof(double)) return NB_ENOMEM;
+  void* scratch = c->d.partials;
+  for (int rep = 0; rep < 2; ++rep) NB_TRY(launch_rate_probe(kind, ctas, iters, scratch, c->st));
+  std::vector<long long> rec(3 * (size_t)ctas);
+  const char* recp = static_cast<const char*>(scratch) + need - rec.size() * sizeof(long long);
+  NB_TRY(cudaMemcpyAsync(rec.data(), recp, rec.size() * sizeof(long long), cudaMemcpyDeviceToHost,
+                         c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));
+  // per SM: its CTAs' operations over the span from first start to last end
+  const double lanes_per_cta = probe_lanes_per_launch(kind, ctas, iters) / ctas;
+  std::vector<long long> lo, hi;
+  std::vector<int> n;
+  std::vector<long long> ids;
+  for (int b = 0; b < ctas; ++b) {
+    const long long sm = rec[3 * b], t0 = rec[3 * b + 1], t1 = rec[3 * b + 2];
+    size_t k = 0;
+    while (k < ids.size() && ids[k] != sm) ++k;
+    if (k == ids.size()) {
+      ids.push_back(sm);
+      lo.push_back(t0);
+      hi.push_back(t1);
+      n.push_back(0);
+    }
+    lo[k] = std::min(lo[k], t0);
+    hi[k] = std::max(hi[k], t1);
+    n[k] += 1;
+  }
+  std::vector<double> rate;
+  for (size_t k = 0; k < ids.size(); ++k)
+    if (hi[k] > lo[k]) rate.push_back(n[k] * lanes_per_cta / (double)(hi[k] - lo[k]));
+  if (rate.empty()) return NB_ECUDA;
+  std::sort(rate.begin(), rate.end());
+  *lanes_per_sm_clock = rate[rate.size() / 2];
+  return NB_OK;
 }
 
 int nb_check_wait_timeout(nb_ctx* c, double seconds) {

@@ -159,6 +159,13 @@ cudaError_t launch_actoff_identity(const Dev& d, cudaStream_t st);
 cudaError_t launch_energy(const Dev& d, const double* pot, int sp, int64_t lo, int64_t hi,
                           double* part, int nblk, double* out, cudaStream_t st);
 
+// arithmetic-rate probe (nb_probe.cu): mode 0 f32x2 FMA, 1 FP32 FMA, 2 FP64 FMA;
+// scratch holds probe_scratch_bytes(ctas); records (smid, start, end clock)
+// per CTA follow ctas * 256 floats
+size_t probe_scratch_bytes(int ctas);
+cudaError_t launch_rate_probe(int mode, int ctas, int iters, void* scratch, cudaStream_t st);
+double probe_lanes_per_launch(int mode, int ctas, int iters);
+
 cudaError_t launch_pack3(const double* src3, dbl4* dst, int64_t n, bool keep_w, cudaStream_t st);
 cudaError_t launch_unpack3(const dbl4* src, double* dst3, int64_t n, cudaStream_t st);
 cudaError_t launch_tcur_from_t(const Dev& d, cudaStream_t st);

@@ -27,7 +27,7 @@ FUNCTIONS = [
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
     "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
     "nb_energies", "nb_autotune", "nb_step_leapfrog", "nb_check_wait_timeout",
-    "nb_noalloc_status",
+    "nb_noalloc_status", "nb_measure_rate",
 ]
 
 
@@ -65,7 +65,7 @@ def _load() -> ctypes.CDLL:
         "nb_predict": (ctypes.c_int, [P, i64]),
         "nb_force": (ctypes.c_int, [P, P, i64, P, P, P]),
         "nb_correct": (ctypes.c_int, [P, i64, P, i64, P, P]),
-        "nb_step_block": (ctypes.c_int, [P, i64]),
+        "nb_step_block": (ctypes.c_int, [P, i64, P, P]),
         "nb_step_leapfrog": (ctypes.c_int, [P, i64, i64]),
         "nb_check_wait_timeout": (ctypes.c_int, [P, ctypes.c_double]),
         "nb_set_end_time": (ctypes.c_int, [P, i64]),
@@ -84,6 +84,7 @@ def _load() -> ctypes.CDLL:
         "nb_force_noalloc": (ctypes.c_int, [P, P, P, i64, P, i64, ctypes.c_double,
                                             ctypes.c_double, i32, P, P, P, P]),
         "nb_noalloc_status": (ctypes.c_int, [P]),
+        "nb_measure_rate": (ctypes.c_int, [P, i32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -228,8 +229,17 @@ class Sim:
         _check(lib.nb_correct(self._ctx, int(t_ticks), _dptr(active), active.numel(),
                               _dptr(acc), _dptr(jerk)), "nb_correct")
 
-    def step(self, n_steps: int = 1):
-        _check(lib.nb_step_block(self._ctx, int(n_steps)), "nb_step_block")
+    def step(self, n_steps: int = 1, report: bool = False):
+        """n_steps block steps (asynchronous).  With ``report`` the call waits
+        and returns (smallest cluster time in ticks, particles corrected in
+        the last step)."""
+        if not report:
+            _check(lib.nb_step_block(self._ctx, int(n_steps), None, None), "nb_step_block")
+            return None
+        t, m = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.nb_step_block(self._ctx, int(n_steps), ctypes.byref(t), ctypes.byref(m)),
+               "nb_step_block")
+        return t.value, m.value
 
     def leapfrog(self, n_steps: int, dt_ticks: int):
         """Kick-drift-kick leapfrog, shared step of ``dt_ticks`` ticks."""
@@ -305,6 +315,13 @@ class Sim:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(lib.nb_tile_stats(self._ctx, ctypes.byref(a), ctypes.byref(b)), "nb_tile_stats")
         return a.value, b.value
+
+    def measure_rate(self, kind: int = 0) -> float:
+        """nb_measure_rate: FMA lanes per SM per clock of this GPU (kind 0:
+        f32x2, 1: FP32, 2: FP64)."""
+        v = ctypes.c_double()
+        _check(lib.nb_measure_rate(self._ctx, int(kind), ctypes.byref(v)), "nb_measure_rate")
+        return v.value
 
     def status(self) -> int:
         return int(lib.nb_status(self._ctx))

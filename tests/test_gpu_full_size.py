@@ -106,6 +106,43 @@ def test_full_size_block_step_sampled(nb, cluster):
     assert np.all(ev <= tol_v), (variant, float((ev / tol_v).max()))
 
 
+def test_full_size_plain_per_particle_error(nb, cluster):
+    """The accuracy target of the mixed path, stated per particle: the plain
+    relative acceleration error ||a - a_ref|| / ||a_ref|| <= 1e-6 for every
+    sampled particle of the N = 2^20 benchmark cluster (512 random targets of
+    nb_force, default kernel shape).  The one exemption is cancellation: a
+    particle whose conditioning kappa = sum_j |a_ij| / |a_i| exceeds 10 has
+    an acceleration much smaller than its terms, and FP32 pair arithmetic
+    bounds its error by a fraction of sum_j |a_ij|, not of |a_i|; such a
+    particle may exceed the plain gate only if it meets the condition-scaled
+    gate, and every particle with kappa > 10 is printed with its errors."""
+    cl = cluster
+    idx = inputs.random_active(N, 512, seed=15)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=EPS, precision=nb.NB_MIXED)
+    try:
+        sim.predict(0)
+        acc, _, _ = sim.force(torch.as_tensor(idx, device="cuda"), want_pot=False)
+        torch.cuda.synchronize()
+        assert sim.status() == nb.NB_OK
+        acc = acc.cpu().numpy()
+    finally:
+        sim.close()
+    ra, _, _ = oracle.force(cl.pos, cl.vel, cl.mass, EPS, idx=idx.astype(np.int64))
+    Sa, _ = term_sums_big(cl.pos, cl.vel, cl.mass, EPS, idx.astype(np.int64))
+    ea = rel_err(acc, ra)
+    kappa = Sa / np.linalg.norm(ra, axis=1)
+    for i in np.flatnonzero(kappa > 10.0):
+        print(f"ill-conditioned particle {idx[i]}: kappa {kappa[i]:.1f}, plain error "
+              f"{ea[i]:.2e}, condition-scaled {ea[i] / kappa[i]:.2e}")
+    # a particle over the plain gate is exempt only when cancellation explains it
+    over = ea > 1e-6
+    assert np.all(kappa[over] > 10.0), (idx[over], ea[over], kappa[over])
+    assert np.all(ea[over] / kappa[over] <= 1e-6)
+    assert over.mean() <= 0.01, over.mean()  # the exemption stays rare
+    print(f"plain acceleration error over {len(idx)} targets: max {ea.max():.2e}, "
+          f"median {np.median(ea):.2e}; {int(over.sum())} over 1e-6 (exempt by kappa)")
+
+
 def test_full_size_fp64_force_sampled(nb, cluster):
     cl = cluster
     idx = inputs.random_active(N, 1024, seed=5)

@@ -281,6 +281,26 @@ def test_block_integration_energy_drift(nb):
     assert abs(drift[nb.NB_MIXED]) <= 2 * abs(drift[nb.NB_FP64]) + 1e-9, (drift, d_ref)
 
 
+def test_step_block_reports_time_and_active_count(nb, plummer1024):
+    """nb_step_block's outputs: the block time after the last step and the
+    number of particles that step corrected, against the state read back."""
+    cl = plummer1024
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, level_min=8, level_max=8)
+    t, m = sim.step(3, report=True)
+    assert t == 3 * sim.ticks(2.0 ** -8) and m == 1024
+    sim.close()
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, level_min=3, level_max=14)
+    sim.step(5)
+    before = sim.get_state()["t"]
+    t, m = sim.step(1, report=True)
+    after = sim.get_state()["t"]
+    assert m == int((after != before).sum()) and m > 0
+    stepped = after != before
+    assert np.all(after[stepped] == t) and np.all(after <= t)
+    assert sim.step(0, report=True) == (t, 0)
+    sim.close()
+
+
 def test_graphs_match_direct_launches(nb):
     cl = inputs.plummer(600, seed=9)
     out = []
