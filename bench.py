@@ -84,7 +84,7 @@ def parse():
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--variant", type=int, default=None, help="mixed force kernel shape")
     p.add_argument("--workload", default="step",
-                   choices=["step", "batch", "drift", "binaries", "leapfrog"],
+                   choices=["step", "batch", "drift", "binaries", "leapfrog", "hermite6"],
                    help="step: the headline line; batch / drift / binaries: the other "
                         "configurations (their own JSON lines)")
     p.add_argument("--clusters", type=int, default=512)
@@ -255,6 +255,96 @@ def workload_leapfrog(args):
         "energy_rel_change": (e1 - e0) / abs(e0),
         "l2": "flushed between timed steps (256 MiB write)"}), flush=True)
     sim.close()
+    return 0
+
+
+# 6th-order convention: the acceleration + jerk convention (38) plus the snap
+# terms counted the same way (FMA = 2 flops): u = a_j - a_i 3, w.w + d.u 11,
+# alpha, beta and the two coefficients 6, u - 6 alpha J' - 3 beta d 12, the
+# accumulation of m/s^3 times it 6
+FLOPS_PER_INTERACTION_SNAP = 76
+LANE_OPS_SNAP = 48          # FP32 lane-operations per interaction in the snap kernel
+
+
+def workload_hermite6(args):
+    """6th-order Hermite block steps (force with snap, Sec. 2 item 1) on the
+    N = 2^20 Kroupa Plummer sphere, every particle on one level (m = N),
+    mixed precision: interactions/s, the snap kernel against the FP32 peak at
+    76 flops and against the FMA pipe at its 48 lane-ops per interaction;
+    FP64 nb_force_snap at m = 2^10; mixed against FP64 on 1024 targets."""
+    import torch
+    from paper_1411_5234_gb300 import inputs, nbody
+    torch.cuda.set_device(0)
+    n, L = args.n, args.level
+    cl = make_cluster(n, 0)
+    sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nbody.NB_MIXED, order=6,
+                    level_min=L, level_max=L, graph_steps=0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sim.step(args.warmup)
+    sim.profile(True)
+    sim.synchronize()
+    sim.profile_read()
+    evs = []
+    with torch.cuda.stream(sim.stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(sim.stream)
+            sim.step(1)
+            ev1.record(sim.stream)
+            evs.append((ev0, ev1))
+    sim.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    force_ms, launches = sim.profile_read()
+    assert sim.status() == nbody.NB_OK
+    rate = args.steps * n * n / (total_ms * 1e-3)
+    per = force_ms * 1e-3 / max(launches, 1)
+    achieved = FLOPS_PER_INTERACTION_SNAP * n * n / per / 1e12
+    peak = fp32_peak_flops() / 1e12
+    pipe = LANE_OPS_SNAP * n * n / per / (sm_count() * FP32_LANES * SM_MAX_MHZ * 1e6)
+    idx = inputs.random_active(n, 1024, seed=9)
+    act = torch.as_tensor(idx, device="cuda")
+    sim.predict(sim.stats().t_min)
+    am, jm, sm, _ = (x.cpu().numpy() for x in sim.force_snap(act))
+    st = sim.get_state()
+    sn, cr = sim.get_derivs()
+    sim.close()
+    # FP64 from the same state: its force with snap on 1024 targets, timed
+    s64 = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nbody.NB_FP64, order=6,
+                    level_min=L, level_max=L, graph_steps=0)
+    s64.set_state(st["pos"], st["vel"], st["acc"], st["jerk"], st["t"], st["level"])
+    s64.set_derivs(sn, cr)
+    s64.predict(int(st["t"][0]))
+    s64.profile(True)
+    s64.force_snap(act)
+    s64.synchronize()
+    s64.profile_read()
+    a6, j6, s6, _ = s64.force_snap(act)
+    ms64, cnt64 = s64.profile_read()
+    a6, j6, s6 = a6.cpu().numpy(), j6.cpu().numpy(), s6.cpu().numpy()
+    s64.close()
+    rel = lambda x, r: np.linalg.norm(x - r, axis=1) / np.linalg.norm(r, axis=1)
+    es, ea = rel(sm, s6), rel(am, a6)
+    print(json.dumps({
+        "workload": f"hermite6 (6th-order block steps, shared level 2^-{L}): Plummer N={n} "
+                    "Kroupa, eps=1e-4, mixed, force with snap",
+        "metric": "pair-interactions/s", "unit": UNIT, "value": rate, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_force_mixed (snap shape)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "flops_per_interaction": FLOPS_PER_INTERACTION_SNAP,
+                     "fma_pipe_frac": pipe, "lane_ops_per_interaction": LANE_OPS_SNAP,
+                     "force_ms_per_launch": per * 1e3,
+                     "force_share_of_step": force_ms / max(total_ms, 1e-9)},
+        "fp64_force_snap": {"m": 1024, "interactions_per_s": 1024 * n / (ms64 / max(cnt64, 1)
+                                                                           * 1e-3)},
+        "mixed_vs_fp64_1024_targets": {
+            "acc_rel_max": float(ea.max()), "acc_rel_median": float(np.median(ea)),
+            "snap_rel_median": float(np.median(es)),
+            "snap_rel_p99": float(np.quantile(es, 0.99))},
+        "l2": "flushed between timed steps (256 MiB write)"}), flush=True)
     return 0
 
 
@@ -479,6 +569,8 @@ def main():
         return workload_drift(args)
     if args.workload == "leapfrog":
         return workload_leapfrog(args)
+    if args.workload == "hermite6":
+        return workload_hermite6(args)
 
     import torch
     from paper_1411_5234_gb300 import inputs, nbody

@@ -102,11 +102,16 @@ typedef struct {
     int32_t variant;    /* shape of the mixed force kernel, 0 .. NB_MIXED_VARIANTS-1
                            (see nb_autotune); all give results of the same
                            accuracy */
+    int32_t order;      /* order of the Hermite scheme: 4 (default) or 6 (the
+                           order of the paper's template code, Sec. 2 item 1):
+                           the force then also yields the snap, the state also
+                           holds snap and crackle, and nb_step_block predicts,
+                           corrects and picks steps with the 6th-order rules */
 } nb_config;
 
 /* Defaults: G = 1, eps = 1e-4, eta = 0.01, eta_start = 0.01, level_min = 0,
  * level_max = 30, tick_exp = 40, NB_MIXED, bfactor = 0, graph_steps = 16,
- * sort_sources = 1, variant = 0. */
+ * sort_sources = 1, variant = 0, order = 4. */
 void nb_default_config(nb_config *cfg);
 
 /* Bytes of the device workspace for n_total particles in n_clusters clusters
@@ -152,6 +157,17 @@ int nb_predict(nb_ctx *ctx, int64_t t_ticks);
 int nb_force(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
              double *jerk, double *pot);
 
+/* Acceleration, jerk, snap and potential for the 6th-order Hermite scheme
+ * (the order of the paper's template code, Sec. 2 item 1): as nb_force, plus
+ * the snap, the second time derivative of the softened pair term of Eq. 2,
+ *   snap_i = G sum_j m_j (u - 6 alpha (w - 3 alpha d) - 3 beta d) / s^3,
+ *   u = a_j - a_i, alpha = d.w / s^2, beta = (w.w + d.u) / s^2 + alpha^2,
+ * with the predicted accelerations a of the last nb_predict.  snap: device
+ * (m x 3) doubles; jerk required; pot may be NULL.  Order-6 contexts only
+ * (NB_ESTATE otherwise).  Asynchronous. */
+int nb_force_snap(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
+                  double *jerk, double *snap, double *pot);
+
 /* Hermite correction (Sec. 2 item 1) of the m particles in active_idx
  * (device, as for nb_force) from their own times to t_ticks, given their new
  * acceleration and jerk evaluated at the predicted state (device m x 3, as
@@ -159,6 +175,20 @@ int nb_force(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
  * from the step criterion.  Asynchronous. */
 int nb_correct(nb_ctx *ctx, int64_t t_ticks, const int32_t *active_idx,
                int64_t m, const double *acc, const double *jerk);
+
+/* 6th-order Hermite correction of the m particles in active_idx from their
+ * own times to t_ticks, given the force with snap at the predicted state
+ * (device m x 3 each, as written by nb_force_snap): over the step t,
+ *   v1 = v0 + t/2 (a0 + a1) - t^2/10 (j1 - j0) + t^3/120 (s0 + s1),
+ *   x1 = x0 + t/2 (v0 + v1) - t^2/10 (a1 - a0) + t^3/120 (j0 + j1)
+ * (the quintic through both ends' a, j, s); keeps the quintic's crackle for
+ * the next prediction and sets a new level from dt = eta (A1 / A4)^(1/3),
+ * A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)| over a, j, s, crackle, pop,
+ * a^(5) at the end of the step.  Order-6 contexts only (nb_correct serves
+ * order 4 and returns NB_ESTATE here).  Asynchronous. */
+int nb_correct_snap(nb_ctx *ctx, int64_t t_ticks, const int32_t *active_idx,
+                    int64_t m, const double *acc, const double *jerk,
+                    const double *snap);
 
 /* Run n_steps block steps (Sec. 2 item 2).  In one block step EVERY cluster
  * whose time is below the end time (nb_set_end_time) independently takes its
@@ -223,6 +253,13 @@ int nb_get_state(nb_ctx *ctx, double *pos, double *vel, double *acc,
 int nb_set_state(nb_ctx *ctx, const double *pos, const double *vel,
                  const double *acc, const double *jerk, const int64_t *t,
                  const int32_t *level);
+
+/* The 6th-order scheme's extra state (order-6 contexts; NB_ESTATE
+ * otherwise): snap and crackle (n x 3 host arrays; get: either may be NULL,
+ * set: both required and finite).  nb_init starts from the snap of the t = 0
+ * force and a zero crackle.  Synchronise. */
+int nb_get_derivs(nb_ctx *ctx, double *snap, double *crackle);
+int nb_set_derivs(nb_ctx *ctx, const double *snap, const double *crackle);
 
 /* Counters since nb_init (host outputs, any may be NULL): block steps taken,
  * pair interactions evaluated (sum over force evaluations of m x N_cluster),

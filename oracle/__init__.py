@@ -85,6 +85,8 @@ def _load():
         lib.oracle_hermite6_correct.restype = None
         lib.oracle_hermite6_dt.argtypes = [P, P, P, P, P, P, f64]
         lib.oracle_hermite6_dt.restype = f64
+        lib.oracle_hermite6_predict.argtypes = [i64] + [P] * 10
+        lib.oracle_hermite6_predict.restype = None
         lib.oracle_hermite6_run.argtypes = [i64, P, P, P, f64, f64, f64, i64]
         lib.oracle_hermite6_run.restype = i32
         lib.oracle_num_threads.argtypes = []
@@ -269,6 +271,19 @@ def hermite6_correct(h, x0, v0, a0, j0, s0, a1, j1, s1):
     h = _f64(np.broadcast_to(np.asarray(h, dtype=np.float64), (m,)))
     out = [np.empty((m, 3)) for _ in range(5)]
     _load().oracle_hermite6_correct(m, _ptr(h), _ptr(x0), *[_ptr(a) for a in args],
+                                    *[_ptr(o) for o in out])
+    return tuple(out)
+
+
+def hermite6_predict(t, x, v, a, j, s, c):
+    """Taylor predictor of the 6th-order scheme over t (scalar or per
+    particle).  Returns ``(x_p, v_p, a_p)``, each (m, 3)."""
+    x = _f64(x).reshape(-1, 3)
+    m = x.shape[0]
+    args = [_f64(y, (m, 3)) for y in (v, a, j, s, c)]
+    t = _f64(np.broadcast_to(np.asarray(t, dtype=np.float64), (m,)))
+    out = [np.empty((m, 3)) for _ in range(3)]
+    _load().oracle_hermite6_predict(m, _ptr(t), _ptr(x), *[_ptr(y) for y in args],
                                     *[_ptr(o) for o in out])
     return tuple(out)
 

@@ -613,6 +613,30 @@ double oracle_hermite6_dt(const double *a, const double *j, const double *s,
     return eta * cbrt(A1 / A4);
 }
 
+/* Taylor predictor of the 6th-order scheme over t (per particle):       */
+/*   x_p = x + v t + a t^2/2 + j t^3/6 + s t^4/24 + c t^5/120,          */
+/*   v_p = v + a t + j t^2/2 + s t^3/6 + c t^4/24,                      */
+/*   a_p = a + j t + s t^2/2 + c t^3/6                                  */
+/* (s snap, c crackle).  m particles, arrays m x 3; t per particle.     */
+/* ------------------------------------------------------------------ */
+void oracle_hermite6_predict(int64_t m, const double *t, const double *x,
+                             const double *v, const double *a, const double *j,
+                             const double *s, const double *c, double *xp,
+                             double *vp, double *ap)
+{
+    for (int64_t k = 0; k < m; k++) {
+        const double h = t[k], h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+        for (int q = 0; q < 3; q++) {
+            const int64_t i = 3 * k + q;
+            xp[i] = x[i] + v[i] * h + a[i] * h2 / 2.0 + j[i] * h3 / 6.0
+                    + s[i] * h4 / 24.0 + c[i] * h5 / 120.0;
+            vp[i] = v[i] + a[i] * h + j[i] * h2 / 2.0 + s[i] * h3 / 6.0
+                    + c[i] * h4 / 24.0;
+            ap[i] = a[i] + j[i] * h + s[i] * h2 / 2.0 + c[i] * h3 / 6.0;
+        }
+    }
+}
+
 /* Shared-step 6th-order Hermite integration of every particle: n_steps */
 /* steps of h.  Start: acc and jerk from oracle_force, snap from        */
 /* oracle_force_snap with those accelerations, crackle zero (the first  */
@@ -647,14 +671,7 @@ int oracle_hermite6_run(int64_t n, double *pos, double *vel,
     oracle_force_snap(n, pos, vel, a, mass, G, eps, n, idx, NULL, NULL, s);
     memset(c, 0, b);
     for (int64_t st = 0; st < n_steps; st++) {
-        const double t = h, t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
-        for (int64_t i = 0; i < 3 * n; i++) {
-            xp[i] = pos[i] + vel[i] * t + a[i] * t2 / 2.0 + j[i] * t3 / 6.0
-                    + s[i] * t4 / 24.0 + c[i] * t5 / 120.0;
-            vp[i] = vel[i] + a[i] * t + j[i] * t2 / 2.0 + s[i] * t3 / 6.0
-                    + c[i] * t4 / 24.0;
-            ap[i] = a[i] + j[i] * t + s[i] * t2 / 2.0 + c[i] * t3 / 6.0;
-        }
+        oracle_hermite6_predict(n, hh, pos, vel, a, j, s, c, xp, vp, ap);
         oracle_force_snap(n, xp, vp, ap, mass, G, eps, n, idx, a1, j1, s1);
         oracle_hermite6_correct(n, hh, pos, vel, a, j, s, a1, j1, s1, pos, vel,
                                 c, NULL, NULL);

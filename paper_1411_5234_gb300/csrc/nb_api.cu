@@ -33,6 +33,7 @@ constexpr size_t kAlign = 256;
 constexpr int kEnergyBlocks = 304;
 
 struct Layout {
+  size_t snap, crackle, snap_new, src_acc_mix, src64_acc;  // 6th order only (else empty)
   size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
       src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, wt_off, wide_cnt, bfac, esum,
       status, counters, t_end, work, tiles, toff, sperm, sinv, mark, rows, total;
@@ -45,8 +46,10 @@ size_t take(size_t& cur, size_t bytes) {
   return o;
 }
 
-Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
+Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles, int order) {
   Layout L{};
+  const bool o6 = order == 6;
+  const int comps = o6 ? kPartialCompsSnap : kPartialComps;
   L.S = S;
   L.n_tiles = n_tiles;
   const int64_t nitile = ceil_div64(N, 128) + K;  // smallest targets-per-item of any shape
@@ -66,7 +69,7 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
   L.src_mix = take(c, 40 * S);
   L.src64_pos = take(c, 32 * S);
   L.src64_vel = take(c, 32 * S);
-  L.partials = take(c, (size_t)L.part_items * kPartialComps * ni_max * 8);
+  L.partials = take(c, (size_t)L.part_items * comps * ni_max * 8);
   L.blk_count = take(c, 4 * ((size_t)n_tiles + 1));
   L.off = take(c, 8 * ((size_t)K + 1));
   L.soff = take(c, 8 * ((size_t)K + 1));
@@ -88,6 +91,11 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles) {
   L.sinv = take(c, 4 * (size_t)N);
   L.mark = take(c, 4 * (size_t)N);
   L.rows = take(c, 4 * (size_t)N);
+  L.snap = take(c, o6 ? 32 * (size_t)N : 0);
+  L.crackle = take(c, o6 ? 32 * (size_t)N : 0);
+  L.snap_new = take(c, o6 ? 32 * (size_t)N : 0);
+  L.src_acc_mix = take(c, o6 ? 12 * (size_t)S : 0);
+  L.src64_acc = take(c, o6 ? 32 * (size_t)S : 0);
   L.total = c;
   return L;
 }
@@ -103,6 +111,7 @@ bool config_ok(const nb_config* c) {
   if (c->bfactor < 0 || c->graph_steps < 0) return false;
   if (c->sort_sources != 0 && c->sort_sources != 1) return false;
   if (c->variant < 0 || c->variant >= force_mixed_variants()) return false;
+  if (c->order != 4 && c->order != 6) return false;
   return true;
 }
 
@@ -196,7 +205,7 @@ struct nb_ctx {
   Dev d;
   Layout L{};
   cudaStream_t st = nullptr;
-  int grid_mix = 0, grid_f64 = 0, grid_acc = 0, sms = 0;
+  int grid_mix = 0, grid_f64 = 0, grid_acc = 0, grid_snap = 0, sms = 0;
   std::vector<int64_t> off_host;
   std::vector<double> mass_host;
   std::vector<int32_t> sperm_host;  // source slot order (for the autotuner's target lists)
@@ -261,14 +270,21 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, doub
   a.eps2 = c->cfg.eps * c->cfg.eps;
   a.status = c->d.status;
   a.work_ctr = c->d.work_ctr;
+  a.src_c = nullptr;
+  a.out_snap = nullptr;
+  a.ss = 0;
+  a.comps = kPartialComps;
   return a;
 }
 
-PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count, bool acc_only = false) {
+PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count, bool acc_only = false,
+                   bool snap = false) {
   PlanArgs p{};
-  p.NI = f64 ? kF64NI : acc_only ? force_mixed_acc_ni() : force_mixed_ni(c->cfg.variant);
+  p.NI = f64 ? kF64NI
+             : snap ? force_mixed_snap_ni()
+                    : acc_only ? force_mixed_acc_ni() : force_mixed_ni(c->cfg.variant);
   p.JT = f64 ? kF64JT : kMixJT;
-  p.grid = f64 ? c->grid_f64 : acc_only ? c->grid_acc : c->grid_mix;
+  p.grid = f64 ? c->grid_f64 : snap ? c->grid_snap : acc_only ? c->grid_acc : c->grid_mix;
   p.forced_b = c->cfg.bfactor;
   p.part_items = c->L.part_items;
   p.step_mode = step_mode;
@@ -359,6 +375,46 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
   return launch_reduce(fa, ni, !pot_only, m_bound, c->sms, c->st);
 }
 
+// plan + force with snap + partial reduce (the 6th-order scheme's force; the
+// sources' predicted accelerations must be in place: an order-6 context's
+// predictor writes them).  snap, ss: the snap rows and their stride.
+cudaError_t enqueue_force_snap(nb_ctx* c, const int32_t* active, const int32_t* rows,
+                               double* acc, int sa, double* jerk, int sj, double* snap, int ss,
+                               double* pot, int sp, int step_mode, int count, int64_t m_bound,
+                               bool planned = false) {
+  const bool f64 = !is_mixed(c);
+  cudaError_t e = cudaSuccess;
+  if (!planned) {
+    e = launch_plan(c->d, plan_args(c, f64, step_mode, count, false, true), c->st);
+    if (e != cudaSuccess) return e;
+  }
+  ForceArgs fa = force_args(c, active, rows, acc, sa, jerk, sj, pot, sp, f64);
+  fa.src_c = f64 ? static_cast<const void*>(c->d.src64_acc)
+                 : static_cast<const void*>(c->d.src_acc_mix);
+  fa.out_snap = snap;
+  fa.ss = ss;
+  fa.comps = kPartialCompsSnap;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (c->prof) {
+    e = prof_events(c, &ev);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev.first, c->st);
+    if (e != cudaSuccess) return e;
+  }
+  if (f64)
+    e = launch_force_fp64(fa, c->grid_f64, kF64Snap, c->st);
+  else
+    e = launch_force_mixed_snap(fa, c->grid_snap, pot != nullptr, c->st);
+  if (e != cudaSuccess) return e;
+  if (c->prof) {
+    e = cudaEventRecord(ev.second, c->st);
+    if (e != cudaSuccess) return e;
+    c->ev_pending.push_back(ev);
+  }
+  const int ni = f64 ? kF64NI : force_mixed_snap_ni();
+  return launch_reduce(fa, ni, true, m_bound, c->sms, c->st);
+}
+
 cudaError_t enqueue_block_step(nb_ctx* c) {
   const int T = c->cfg.tick_exp;
   const bool f64 = !is_mixed(c);
@@ -366,10 +422,35 @@ cudaError_t enqueue_block_step(nb_ctx* c) {
   if (e != cudaSuccess) return e;
   e = launch_predict(c->d, c->d.t_min, 0, T, !f64, f64, true, c->st);
   if (e != cudaSuccess) return e;
-  e = launch_scan_plan_scatter(c->d, plan_args(c, f64, 1, 1), T, c->st);
+  const bool o6 = c->cfg.order == 6;
+  e = launch_scan_plan_scatter(c->d, plan_args(c, f64, 1, 1, false, o6), T, c->st);
   if (e != cudaSuccess) return e;
   double* an = reinterpret_cast<double*>(c->d.acc_new);
   double* jn = reinterpret_cast<double*>(c->d.jerk_new);
+  if (o6) {
+    double* sn = reinterpret_cast<double*>(c->d.snap_new);
+    e = enqueue_force_snap(c, c->d.active, nullptr, an, 4, jn, 4, sn, 4, nullptr, 0, 1, 1,
+                           c->d.N, true);
+    if (e != cudaSuccess) return e;
+    CorrectArgs ca{};
+    ca.active = c->d.active;
+    ca.count_dev = c->d.act_off + c->d.K;
+    ca.acc = an;
+    ca.sa = 4;
+    ca.jerk = jn;
+    ca.sj = 4;
+    ca.snap = sn;
+    ca.ss = 4;
+    ca.pot = nullptr;
+    ca.sp = 0;
+    ca.t_tgt = c->d.t_cur;
+    ca.eta = c->cfg.eta;
+    ca.T = T;
+    ca.lmin = c->cfg.level_min;
+    ca.lmax = c->cfg.level_max;
+    ca.reset_tmin = 1;
+    return launch_correct6(c->d, ca, c->d.N, c->st);
+  }
   // the integrator needs no potential: the force kernel skips it here
   e = enqueue_force(c, c->d.active, nullptr, an, 4, jn, 4, nullptr, 0, f64, 1, 1, false,
                     c->d.N, true);
@@ -428,6 +509,7 @@ void nb_default_config(nb_config* cfg) {
   cfg->graph_steps = 16;
   cfg->sort_sources = 1;
   cfg->variant = kMixDefaultVariant;
+  cfg->order = 4;
 }
 
 int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config* cfg, size_t* bytes) {
@@ -437,7 +519,7 @@ int nb_workspace_size(int64_t n_total, int32_t n_clusters, const nb_config* cfg,
   // worst case of the slot padding (3 pad slots per cluster) and of the
   // tile count (one partial tile per cluster)
   const int64_t S = n_total + 3 * (int64_t)n_clusters;
-  *bytes = make_layout(n_total, n_clusters, S, S / kMixJT + n_clusters).total;
+  *bytes = make_layout(n_total, n_clusters, S, S / kMixJT + n_clusters, cfg->order).total;
   return NB_OK;
 }
 
@@ -470,7 +552,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   c->mass_host.assign(mass, mass + N);
   const int64_t S = slots_of(offsets, n_clusters);
   const int64_t n_tiles = tiles_of(offsets, n_clusters);
-  c->L = make_layout(N, n_clusters, S, n_tiles);
+  c->L = make_layout(N, n_clusters, S, n_tiles, cfg->order);
   char* w = static_cast<char*>(workspace);
   Dev& d = c->d;
   d.N = N;
@@ -506,6 +588,14 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   d.counters = reinterpret_cast<unsigned long long*>(w + c->L.counters);
   d.t_end = reinterpret_cast<int64_t*>(w + c->L.t_end);
   d.work_ctr = reinterpret_cast<int32_t*>(w + c->L.work);
+  d.order = cfg->order;
+  if (cfg->order == 6) {
+    d.snap = reinterpret_cast<dbl4*>(w + c->L.snap);
+    d.crackle = reinterpret_cast<dbl4*>(w + c->L.crackle);
+    d.snap_new = reinterpret_cast<dbl4*>(w + c->L.snap_new);
+    d.src_acc_mix = reinterpret_cast<float4*>(w + c->L.src_acc_mix);
+    d.src64_acc = reinterpret_cast<dbl4*>(w + c->L.src64_acc);
+  }
   d.tiles = reinterpret_cast<float4*>(w + c->L.tiles);
   d.toff = reinterpret_cast<int32_t*>(w + c->L.toff);
   d.n_tiles = n_tiles;
@@ -524,6 +614,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
                             : sms * force_mixed_ctas_per_sm(c->cfg.variant);
   c->grid_f64 = sms * force_fp64_ctas_per_sm();
   c->grid_acc = sms * force_mixed_acc_ctas_per_sm();
+  c->grid_snap = sms * force_mixed_snap_ctas_per_sm();
   c->sms = sms;
   if (integrator_setup() != cudaSuccess) {
     delete c;
@@ -569,7 +660,9 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
         cudaMemsetAsync(d.t_cur, 0, 8 * n_clusters, st) ||
         cudaMemsetAsync(d.status, 0, 4, st) || cudaMemsetAsync(d.counters, 0, 32, st) ||
         cudaMemsetAsync(d.wide_cnt, 0, 4 * (size_t)wide_counter_entries(c->L.part_items), st) ||
-        cudaMemsetAsync(d.mark, 0xff, 4 * N, st)) {
+        cudaMemsetAsync(d.mark, 0xff, 4 * N, st) ||
+        (cfg->order == 6 && (cudaMemsetAsync(d.snap, 0, 32 * N, st) ||
+                             cudaMemsetAsync(d.crackle, 0, 32 * N, st)))) {
       rc = NB_ECUDA;
       break;
     }
@@ -587,6 +680,18 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
         launch_init_levels(d, cfg->eta_start, cfg->tick_exp, cfg->level_min, cfg->level_max, st)) {
       rc = NB_ECUDA;
       break;
+    }
+    if (cfg->order == 6) {
+      // snap at t = 0 from the sources' accelerations a0 (the predictor at
+      // tau = 0 writes them; snap and crackle were zeroed above, and the
+      // crackle stays zero): the start of the 6th-order scheme
+      if (launch_predict(d, nullptr, 0, cfg->tick_exp, !f64, f64, false, st, true) ||
+          launch_slot_list(d, st) || launch_actoff_identity(d, st) ||
+          enqueue_force_snap(c, d.active, d.active, an, 4, jn, 4,
+                             reinterpret_cast<double*>(d.snap), 4, nullptr, 0, 0, 0, N)) {
+        rc = NB_ECUDA;
+        break;
+      }
     }
     rc = sync_status(c);
   } while (false);
@@ -632,10 +737,86 @@ int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, doubl
   return NB_OK;
 }
 
+int nb_force_snap(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, double* jerk,
+                  double* snap, double* pot) {
+  NvtxRange nvtx_range("nb_force_snap");
+  if (!c || m < 0 || m > c->d.N) return NB_EINVAL;
+  if (c->cfg.order != 6) return NB_ESTATE;
+  if (m == 0) return NB_OK;
+  if (!active_idx || !acc || !jerk || !snap) return NB_EINVAL;
+  NB_TRY(launch_list_to_slots(c->d, active_idx, m, c->st));
+  NB_TRY(enqueue_force_snap(c, c->d.active, c->d.rows, acc, 3, jerk, 3, snap, 3, pot, 1, 0, 1,
+                            m));
+  return NB_OK;
+}
+
+int nb_correct_snap(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
+                    const double* acc, const double* jerk, const double* snap) {
+  NvtxRange nvtx_range("nb_correct_snap");
+  if (!c || m < 0 || m > c->d.N || t_ticks < 0) return NB_EINVAL;
+  if (c->cfg.order != 6) return NB_ESTATE;
+  if (m == 0) return NB_OK;
+  if (!active_idx || !acc || !jerk || !snap) return NB_EINVAL;
+  CorrectArgs ca{};
+  ca.active = active_idx;
+  ca.count_dev = nullptr;
+  ca.count_host = m;
+  ca.acc = acc;
+  ca.sa = 3;
+  ca.jerk = jerk;
+  ca.sj = 3;
+  ca.snap = snap;
+  ca.ss = 3;
+  ca.pot = nullptr;
+  ca.t_tgt = nullptr;
+  ca.t_fixed = t_ticks;
+  ca.eta = c->cfg.eta;
+  ca.T = c->cfg.tick_exp;
+  ca.lmin = c->cfg.level_min;
+  ca.lmax = c->cfg.level_max;
+  NB_TRY(launch_correct6(c->d, ca, m, c->st));
+  return NB_OK;
+}
+
+int nb_get_derivs(nb_ctx* c, double* snap, double* crackle) {
+  NvtxRange nvtx_range("nb_get_derivs");
+  if (!c) return NB_EINVAL;
+  if (c->cfg.order != 6) return NB_ESTATE;
+  const int64_t N = c->d.N;
+  const dbl4* srcs[2] = {c->d.snap, c->d.crackle};
+  double* dsts[2] = {snap, crackle};
+  double* stage[2] = {reinterpret_cast<double*>(c->d.acc_new),
+                      reinterpret_cast<double*>(c->d.jerk_new)};
+  for (int q = 0; q < 2; ++q) {
+    if (!dsts[q]) continue;
+    NB_TRY(launch_unpack3(srcs[q], stage[q], N, c->st));
+    NB_TRY(cudaMemcpyAsync(dsts[q], stage[q], 24 * N, cudaMemcpyDeviceToHost, c->st));
+  }
+  NB_TRY(cudaStreamSynchronize(c->st));
+  return NB_OK;
+}
+
+int nb_set_derivs(nb_ctx* c, const double* snap, const double* crackle) {
+  NvtxRange nvtx_range("nb_set_derivs");
+  if (!c || !snap || !crackle) return NB_EINVAL;
+  if (c->cfg.order != 6) return NB_ESTATE;
+  const int64_t N = c->d.N;
+  if (!finite_all(snap, 3 * N) || !finite_all(crackle, 3 * N)) return NB_EINVAL;
+  double* sa = reinterpret_cast<double*>(c->d.acc_new);
+  double* sb = reinterpret_cast<double*>(c->d.jerk_new);
+  NB_TRY(cudaMemcpyAsync(sa, snap, 24 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(cudaMemcpyAsync(sb, crackle, 24 * N, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(launch_pack3(sa, c->d.snap, N, false, c->st));
+  NB_TRY(launch_pack3(sb, c->d.crackle, N, false, c->st));
+  NB_TRY(cudaStreamSynchronize(c->st));
+  return NB_OK;
+}
+
 int nb_correct(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
                const double* acc, const double* jerk) {
   NvtxRange nvtx_range("nb_correct");
   if (!c || m < 0 || m > c->d.N || t_ticks < 0) return NB_EINVAL;
+  if (c->cfg.order == 6) return NB_ESTATE;
   if (m == 0) return NB_OK;
   if (!active_idx || !acc || !jerk) return NB_EINVAL;
   CorrectArgs ca{};

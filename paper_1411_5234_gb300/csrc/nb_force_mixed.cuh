@@ -85,12 +85,15 @@ enum { cDXH = 0, cDYH, cDZH, cM, cVX, cVY, cVZ, cDXL, cDYL, cDZL };
 enum { kSepMixed = 0, kSepDS = 1, kSepFP32 = 2 };
 
 template <int NT_, int IPT_, bool POT_, bool RCP_, bool SMT_, int UNR_, int MINB_,
-          bool JERK_ = true, int SEP_ = kSepMixed, int NU_ = 1, int ST_ = 1>
+          bool JERK_ = true, int SEP_ = kSepMixed, int NU_ = 1, int ST_ = 1, bool SNAP_ = false>
 struct MixShape {
   static constexpr int NT = NT_, IPT = IPT_, NI = NT_ * IPT_, UNR = UNR_, MINB = MINB_;
-  static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_, JERK = JERK_;
+  static constexpr bool POT = POT_, RCP = RCP_, SMT = SMT_, JERK = JERK_, SNAP = SNAP_;
   static constexpr int SEP = SEP_, NU = NU_, ST = ST_;
+  // compensated totals (and partial-sum components) per target
+  static constexpr int TC = SNAP_ ? kPartialCompsSnap : kPartialComps;
   static_assert(NT_ * IPT_ <= kMixNI, "partial-sum rows hold at most kMixNI targets");
+  static_assert(!SNAP_ || JERK_, "the snap needs the jerk terms");
 };
 
 // What the source loop needs of one target in registers; the target's
@@ -98,11 +101,13 @@ struct MixShape {
 struct Target {
   f2 nvx, nvy, nvz;              // -v_i as broadcast pairs
   f2 ex, ey, ez;                 // hi part of c_J - r_i (broadcast)
-  f2 ax, ay, az, jx, jy, jz, pt; // per-tile sums (2 lanes)
+  f2 ax, ay, az, jx, jy, jz, pt; // per-stage sums (2 lanes)
+  f2 nax, nay, naz;              // snap shapes: -a_i (the predicted acceleration)
+  f2 sx, sy, sz;                 // snap shapes: per-stage snap sums
 };
 
-// compensated totals per target: a (3), jerk (3), potential
-constexpr int kTotComps = 7;
+// compensated totals per target: a (3), jerk (3), potential, [snap (3)]
+constexpr int kTotComps = kPartialCompsSnap;
 
 // Per-thread shared-memory record of a target: r_i as double-single and its
 // source slot (-1: no target); component-major so a warp's loads are
@@ -148,9 +153,14 @@ __device__ __forceinline__ void ds_sub0(float c, float bh, float bl, float& rh, 
 
 // Shared tail of one pair step: from the separation d, relative velocity w
 // to the accumulators.
+// Snap shapes also take u = a_j - a_i and add the snap term
+// m (u - 6 alpha (w - 3 alpha d) - 3 beta d) / s^3, alpha = d.w / s^2,
+// beta = (w.w + d.u) / s^2 + alpha^2 (the second time derivative of the pair
+// term of Eq. 2; 22 more FP32 lane-ops per interaction).
 template <class Sh, bool MASK>
 __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx, f2 wy, f2 wz,
-                                          f2 m, f2 eps2, int64_t js, int64_t slot) {
+                                          f2 ux, f2 uy, f2 uz, f2 m, f2 eps2, int64_t js,
+                                          int64_t slot) {
   f2 r2 = f2_fma(dx, dx, eps2);
   r2 = f2_fma(dy, dy, r2);
   r2 = f2_fma(dz, dz, r2);
@@ -170,7 +180,29 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
   s.ax = f2_fma(mr3, dx, s.ax);
   s.ay = f2_fma(mr3, dy, s.ay);
   s.az = f2_fma(mr3, dz, s.az);
-  if constexpr (Sh::JERK) {
+  if constexpr (Sh::SNAP) {
+    f2 rv = f2_mul(dx, wx);
+    rv = f2_fma(dy, wy, rv);
+    rv = f2_fma(dz, wz, rv);
+    f2 wdu = f2_mul(wx, wx);  // w.w + d.u
+    wdu = f2_fma(wy, wy, wdu);
+    wdu = f2_fma(wz, wz, wdu);
+    wdu = f2_fma(dx, ux, wdu);
+    wdu = f2_fma(dy, uy, wdu);
+    wdu = f2_fma(dz, uz, wdu);
+    const f2 r2m3 = f2_mul(r2inv, f2_pack(-3.f, -3.f));
+    const f2 t = f2_mul(rv, r2m3);                 // -3 alpha
+    const f2 alpha = f2_mul(rv, r2inv);
+    const f2 c2 = f2_fma(alpha, t, f2_mul(wdu, r2m3));  // -3 beta
+    const f2 c1 = f2_add(t, t);                    // -6 alpha
+    const f2 jx = f2_fma(t, dx, wx), jy = f2_fma(t, dy, wy), jz = f2_fma(t, dz, wz);
+    s.jx = f2_fma(mr3, jx, s.jx);
+    s.jy = f2_fma(mr3, jy, s.jy);
+    s.jz = f2_fma(mr3, jz, s.jz);
+    s.sx = f2_fma(mr3, f2_fma(c2, dx, f2_fma(c1, jx, ux)), s.sx);
+    s.sy = f2_fma(mr3, f2_fma(c2, dy, f2_fma(c1, jy, uy)), s.sy);
+    s.sz = f2_fma(mr3, f2_fma(c2, dz, f2_fma(c1, jz, uz)), s.sz);
+  } else if constexpr (Sh::JERK) {
     f2 rv = f2_mul(dx, wx);
     rv = f2_fma(dy, wy, rv);
     rv = f2_fma(dz, wz, rv);
@@ -178,13 +210,20 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
     s.jx = f2_fma(mr3, f2_fma(t, dx, wx), s.jx);
     s.jy = f2_fma(mr3, f2_fma(t, dy, wy), s.jy);
     s.jz = f2_fma(mr3, f2_fma(t, dz, wz), s.jz);
+    (void)ux; (void)uy; (void)uz;
   }
 }
+
+// Source accelerations of the snap shapes: 3 float4 per group of 4 slots
+// ([ax][ay][az]), beside the group's 10 float4.
+constexpr int kAccGroupF4 = 3;
+constexpr int kAccTileF4 = JT / 4 * kAccGroupF4;
 
 // Far cell: d = dh_j + eh.  NG > 0: a full cell with a compile-time trip
 // count (no remainder code, better interleaving); NG == 0: ngroups groups.
 template <class Sh, int NG = 0>
-__device__ __forceinline__ void tile_far(const float4* __restrict__ tile, int ngroups,
+__device__ __forceinline__ void tile_far(const float4* __restrict__ tile,
+                                         const float4* __restrict__ acc, int ngroups,
                                          Target (&tg)[Sh::IPT], f2 eps2) {
   const int n = NG > 0 ? NG : ngroups;
 #pragma unroll Sh::UNR
@@ -192,15 +231,25 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ tile, int ng
     const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
                      vy = G[cVY], vz = G[cVZ];
+    ulonglong2 ax{0ull, 0ull}, ay{0ull, 0ull}, az{0ull, 0ull};
+    if constexpr (Sh::SNAP) {
+      const ulonglong2* A = reinterpret_cast<const ulonglong2*>(acc + g * kAccGroupF4);
+      ax = A[0];
+      ay = A[1];
+      az = A[2];
+    }
 #pragma unroll
     for (int r = 0; r < Sh::IPT; ++r) {
       Target& s = tg[r];
+      const bool sn = Sh::SNAP;
       pair_tail<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
-                           f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
-                           eps2, 0, -1);
+                           f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz),
+                           sn ? f2_add(ax.x, s.nax) : 0ull, sn ? f2_add(ay.x, s.nay) : 0ull,
+                           sn ? f2_add(az.x, s.naz) : 0ull, m.x, eps2, 0, -1);
       pair_tail<Sh, false>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
-                           f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
-                           eps2, 0, -1);
+                           f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz),
+                           sn ? f2_add(ax.y, s.nax) : 0ull, sn ? f2_add(ay.y, s.nay) : 0ull,
+                           sn ? f2_add(az.y, s.naz) : 0ull, m.y, eps2, 0, -1);
     }
   }
 }
@@ -210,7 +259,8 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ tile, int ng
 // one target's low parts are live at a time.  (Plain FP32 separation mode:
 // d = dh_j + eh, the low words unused.)
 template <class Sh, bool MASK>
-__device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile, int ngroups,
+__device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile,
+                                              const float4* __restrict__ acc, int ngroups,
                                               int64_t slot0, Target& s, f2 elx, f2 ely, f2 elz,
                                               int64_t slot, f2 eps2) {
 #pragma unroll Sh::NU
@@ -218,25 +268,38 @@ __device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile, i
     const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
                      vy = G[cVY], vz = G[cVZ], dxl = G[cDXL], dyl = G[cDYL], dzl = G[cDZL];
+    f2 ux0 = 0ull, uy0 = 0ull, uz0 = 0ull, ux1 = 0ull, uy1 = 0ull, uz1 = 0ull;
+    if constexpr (Sh::SNAP) {
+      const ulonglong2* A = reinterpret_cast<const ulonglong2*>(acc + g * kAccGroupF4);
+      const ulonglong2 ax = A[0], ay = A[1], az = A[2];
+      ux0 = f2_add(ax.x, s.nax);
+      uy0 = f2_add(ay.x, s.nay);
+      uz0 = f2_add(az.x, s.naz);
+      ux1 = f2_add(ax.y, s.nax);
+      uy1 = f2_add(ay.y, s.nay);
+      uz1 = f2_add(az.y, s.naz);
+    }
     const int64_t js = slot0 + 4 * g;
     if constexpr (Sh::SEP == kSepFP32) {
       pair_tail<Sh, MASK>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
-                          f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
-                          eps2, js, slot);
+                          f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), ux0,
+                          uy0, uz0, m.x, eps2, js, slot);
       pair_tail<Sh, MASK>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
-                          f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
-                          eps2, js + 2, slot);
+                          f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), ux1,
+                          uy1, uz1, m.y, eps2, js + 2, slot);
       (void)dxl; (void)dyl; (void)dzl; (void)elx; (void)ely; (void)elz;
       continue;
     }
     pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.x, s.ex), f2_add(dxl.x, elx)),
                         f2_add(f2_add(dyh.x, s.ey), f2_add(dyl.x, ely)),
                         f2_add(f2_add(dzh.x, s.ez), f2_add(dzl.x, elz)), f2_add(vx.x, s.nvx),
-                        f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x, eps2, js, slot);
+                        f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), ux0, uy0, uz0, m.x, eps2, js,
+                        slot);
     pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.y, s.ex), f2_add(dxl.y, elx)),
                         f2_add(f2_add(dyh.y, s.ey), f2_add(dyl.y, ely)),
                         f2_add(f2_add(dzh.y, s.ez), f2_add(dzl.y, elz)), f2_add(vx.y, s.nvx),
-                        f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y, eps2, js + 2, slot);
+                        f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), ux1, uy1, uz1, m.y, eps2,
+                        js + 2, slot);
   }
 }
 
@@ -246,24 +309,24 @@ __device__ __forceinline__ float lanes_sum(f2& v) {
   return p.x + p.y;
 }
 
-// Compensated totals of one target: kTotComps (hi, lo) pairs, in registers
-// or in shared memory (one column per thread).
-template <bool SMT, int NT>
+// Compensated totals of one target: TC (hi, lo) pairs, in registers or in
+// shared memory (one column per thread).
+template <bool SMT, int NT, int TC>
 struct Totals {
-  float h[kTotComps], l[kTotComps];
+  float h[TC], l[TC];
   __device__ __forceinline__ void zero(float*) {
 #pragma unroll
-    for (int c = 0; c < kTotComps; ++c) h[c] = l[c] = 0.f;
+    for (int c = 0; c < TC; ++c) h[c] = l[c] = 0.f;
   }
   __device__ __forceinline__ void add(float*, int c, float x) { two_sum_acc(h[c], l[c], x); }
   __device__ __forceinline__ double get(float*, int c) const { return (double)h[c] + (double)l[c]; }
 };
-template <int NT>
-struct Totals<true, NT> {
+template <int NT, int TC>
+struct Totals<true, NT, TC> {
   // column of this thread: col[(2 c) NT] = hi, col[(2 c + 1) NT] = lo
   __device__ __forceinline__ void zero(float* col) {
 #pragma unroll
-    for (int c = 0; c < 2 * kTotComps; ++c) col[c * NT] = 0.f;
+    for (int c = 0; c < 2 * TC; ++c) col[c * NT] = 0.f;
   }
   // components c, c + 1 at once: packed two-sum of x = (x_c, x_c+1)
   __device__ __forceinline__ void add2(float* col, int c, f2 x) {
@@ -298,7 +361,8 @@ __device__ __forceinline__ f2 lanes_sum2(f2& a, f2& b) {
 }
 
 template <class Sh>
-__device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT>& T, float* col) {
+__device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT, Sh::TC>& T,
+                                      float* col) {
   if constexpr (!Sh::JERK) {  // acceleration (and potential) only
     if constexpr (Sh::SMT) {
       T.add2(col, 0, lanes_sum2(s.ax, s.ay));
@@ -319,19 +383,32 @@ __device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT>& T, flo
     T.add(col, 4, lanes_sum(s.jy));
     T.add(col, 5, lanes_sum(s.jz));
   }
+  if constexpr (Sh::SNAP) {
+    if constexpr (Sh::SMT) {
+      T.add2(col, 7, lanes_sum2(s.sx, s.sy));
+    } else {
+      T.add(col, 7, lanes_sum(s.sx));
+      T.add(col, 8, lanes_sum(s.sy));
+    }
+    T.add(col, 9, lanes_sum(s.sz));
+  }
   if (Sh::POT) T.add(col, 6, lanes_sum(s.pt));
 }
 
 // Slots t0 .. t0 + cnt (cnt a multiple of 4, at most a stage) plus the cell
 // records (centre, radius) of the tiles they span; t0 starts a tile.
-__device__ __forceinline__ void issue_tile(float4* stage, float4* rec, uint64_t* bar,
-                                           const float4* src, const float4* tiles,
-                                           int64_t t0, int64_t cnt, int64_t tile_idx) {
+// Snap shapes (acc != nullptr) also copy the slots' accelerations.
+__device__ __forceinline__ void issue_tile(float4* stage, float4* rec, float4* stage_acc,
+                                           uint64_t* bar, const float4* src, const float4* tiles,
+                                           const float4* acc, int64_t t0, int64_t cnt,
+                                           int64_t tile_idx) {
   const uint32_t bytes = static_cast<uint32_t>(cnt / 4) * kGroupBytes;
   const uint32_t rec_bytes = 16u * kTileRecF4 * static_cast<uint32_t>(ceil_div64(cnt, JT));
-  mbar_arrive_expect(bar, bytes + rec_bytes);
+  const uint32_t acc_bytes = acc ? static_cast<uint32_t>(cnt / 4) * 16u * kAccGroupF4 : 0u;
+  mbar_arrive_expect(bar, bytes + rec_bytes + acc_bytes);
   bulk_g2s(stage, src + (t0 >> 2) * kGroupF4, bytes, bar);
   bulk_g2s(rec, tiles + kTileRecF4 * tile_idx, rec_bytes, bar);
+  if (acc) bulk_g2s(stage_acc, acc + (t0 >> 2) * kAccGroupF4, acc_bytes, bar);
 }
 
 template <class Sh>
@@ -343,7 +420,9 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int abort_flag;
   __shared__ int32_t item_sh;
-  __shared__ float tot_sh[Sh::SMT ? IPT * 2 * kTotComps * NT : 1];
+  constexpr int TC = Sh::TC;
+  __shared__ __align__(16) float4 stage_acc[Sh::SNAP ? 2 : 1][Sh::SNAP ? Sh::ST * kAccTileF4 : 1];
+  __shared__ float tot_sh[Sh::SMT ? IPT * 2 * TC * NT : 1];
   __shared__ TargetPosSh<IPT, NT> tpos;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -357,6 +436,8 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
   bool pending[2] = {false, false};
   const float4* __restrict__ src = static_cast<const float4*>(a.src_a);
   const float4* __restrict__ tiles = a.tiles;
+  // snap shapes: the sources' predicted accelerations (3 float4 per group)
+  const float4* __restrict__ gacc = Sh::SNAP ? static_cast<const float4*>(a.src_c) : nullptr;
   const float e2 = static_cast<float>(a.eps2);
   const f2 eps2 = f2_pack(e2, e2);
   const int32_t n_items = a.item_off[a.K];
@@ -381,7 +462,7 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
     const int64_t p0 = a.off[k], p1 = a.off[k + 1];
 
     Target tg[IPT];
-    Totals<Sh::SMT, NT> tot[IPT];
+    Totals<Sh::SMT, NT, TC> tot[IPT];
     bool valid[IPT];
     // warp wp owns the 32 * IPT consecutive targets [wp * 32 * IPT, ...):
     // target r of lane ln is wp * 32 * IPT + r * 32 + ln (spatially compact
@@ -392,7 +473,7 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       const int32_t q = it * NI + wp * 32 * IPT + r * 32 + ln;
       valid[r] = q < m_k;
       float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f, vx = 0.f, vy = 0.f,
-            vz = 0.f;
+            vz = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
       long long slot_r = -1;
       if (valid[r]) {
         const int32_t s = a0 + q;
@@ -414,6 +495,13 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
           vx = gp[4 * cVX];
           vy = gp[4 * cVY];
           vz = gp[4 * cVZ];
+          if constexpr (Sh::SNAP) {
+            const float* ga =
+                reinterpret_cast<const float*>(gacc + (slot >> 2) * kAccGroupF4) + (slot & 3);
+            ax = ga[0];
+            ay = ga[4];
+            az = ga[8];
+          }
           slot_r = slot;
         }
       }
@@ -428,19 +516,21 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       tg[r].ax = tg[r].ay = tg[r].az = 0ull;
       tg[r].jx = tg[r].jy = tg[r].jz = 0ull;
       tg[r].pt = 0ull;
-      tot[r].zero(tot_sh + r * 2 * kTotComps * NT + tid);
+      tg[r].nax = bcast(-ax); tg[r].nay = bcast(-ay); tg[r].naz = bcast(-az);
+      tg[r].sx = tg[r].sy = tg[r].sz = 0ull;
+      tot[r].zero(tot_sh + r * 2 * TC * NT + tid);
     }
 
     // pipeline stages of SJ slots (the chunk starts on a tile boundary)
     const int64_t ntile = ceil_div64(j1 - j0, SJ);
     uint32_t n_near = 0;  // cells this warp took on the near path
     if (tid == 0) {
-      issue_tile(stage[0], rec[0], &bar[0], src, tiles, j0, min((int64_t)SJ, j1 - j0),
-                 tk0 + (j0 - sk0) / JT);
+      issue_tile(stage[0], rec[0], stage_acc[0], &bar[0], src, tiles, gacc, j0,
+                 min((int64_t)SJ, j1 - j0), tk0 + (j0 - sk0) / JT);
       pending[0] = true;
       if (ntile > 1) {
-        issue_tile(stage[1], rec[1], &bar[1], src, tiles, j0 + SJ,
-                   min((int64_t)SJ, j1 - j0 - SJ), tk0 + (j0 - sk0) / JT + Sh::ST);
+        issue_tile(stage[1], rec[1], stage_acc[Sh::SNAP ? 1 : 0], &bar[1], src, tiles, gacc,
+                   j0 + SJ, min((int64_t)SJ, j1 - j0 - SJ), tk0 + (j0 - sk0) / JT + Sh::ST);
         pending[1] = true;
       }
     }
@@ -482,6 +572,7 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
           far = far && (!valid[r] || d2 > far_lim);
         }
         const float4* cell = stage[st] + g0 * kGroupF4;
+        const float4* cacc = Sh::SNAP ? stage_acc[st] + g0 * kAccGroupF4 : nullptr;
         const int64_t c0 = t0 + 4 * g0;
         bool take_far;
         if constexpr (Sh::SEP == kSepMixed) {
@@ -499,9 +590,9 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
         }
         if (take_far) {
           if (ngq == kCellGroups)
-            tile_far<Sh, kCellGroups>(cell, ngq, tg, eps2);
+            tile_far<Sh, kCellGroups>(cell, cacc, ngq, tg, eps2);
           else
-            tile_far<Sh>(cell, ngq, tg, eps2);
+            tile_far<Sh>(cell, cacc, ngq, tg, eps2);
         } else {
           ++n_near;
 #pragma unroll
@@ -512,20 +603,21 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
             ds_sub0(ch.y, tp.yh, tp.yl, h, ly);
             ds_sub0(ch.z, tp.zh, tp.zl, h, lz);
             // the slot test excludes j == i where the target's own cell is near
-            tile_near_one<Sh, true>(cell, ngq, c0, tg[r], bcast(lx), bcast(ly), bcast(lz),
-                                    tp.slot, eps2);
+            tile_near_one<Sh, true>(cell, cacc, ngq, c0, tg[r], bcast(lx), bcast(ly),
+                                    bcast(lz), tp.slot, eps2);
           }
         }
       }
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < IPT; ++r) flush<Sh>(tg[r], tot[r], tot_sh + r * 2 * kTotComps * NT + tid);
+        for (int r = 0; r < IPT; ++r) flush<Sh>(tg[r], tot[r], tot_sh + r * 2 * TC * NT + tid);
       }
       __syncthreads();
       if (abort_flag) goto drain;
       if (tid == 0 && t + 2 < ntile) {
-        issue_tile(stage[st], rec[st], &bar[st], src, tiles, t0 + 2 * SJ,
-                   min((int64_t)SJ, j1 - t0 - 2 * SJ), tk0 + (t0 - sk0) / JT + 2 * Sh::ST);
+        issue_tile(stage[st], rec[st], stage_acc[Sh::SNAP ? st : 0], &bar[st], src, tiles, gacc,
+                   t0 + 2 * SJ, min((int64_t)SJ, j1 - t0 - 2 * SJ),
+                   tk0 + (t0 - sk0) / JT + 2 * Sh::ST);
         pending[st] = true;
       }
     }
@@ -537,8 +629,8 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
 #pragma unroll
     for (int r = 0; r < IPT; ++r) {
       if (!valid[r]) continue;
-      float* col = tot_sh + r * 2 * kTotComps * NT + tid;
-      double v[kPartialComps];
+      float* col = tot_sh + r * 2 * TC * NT + tid;
+      double v[TC];
       v[0] = tot[r].get(col, 0);
       v[1] = tot[r].get(col, 1);
       v[2] = tot[r].get(col, 2);
@@ -546,6 +638,11 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       v[4] = Sh::JERK ? tot[r].get(col, 4) : 0.0;
       v[5] = Sh::JERK ? tot[r].get(col, 5) : 0.0;
       v[6] = Sh::POT ? -tot[r].get(col, 6) : 0.0;
+      if constexpr (Sh::SNAP) {
+        v[7] = tot[r].get(col, 7);
+        v[8] = tot[r].get(col, 8);
+        v[9] = tot[r].get(col, 9);
+      }
       const int32_t ql = wp * 32 * IPT + r * 32 + ln;
       if (B == 1) {
         int64_t srow = a0 + it * NI + ql;
@@ -554,10 +651,14 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
         if (Sh::JERK && a.out_jerk)
           for (int c = 0; c < 3; ++c) a.out_jerk[srow * a.sj + c] = a.G * v[3 + c];
         if (Sh::POT && a.out_pot) a.out_pot[srow * a.sp] = a.G * v[6];
+        if constexpr (Sh::SNAP) {
+          if (a.out_snap)
+            for (int c = 0; c < 3; ++c) a.out_snap[srow * a.ss + c] = a.G * v[kPartialComps + c];
+        }
       } else {
-        double* P = a.partials + (size_t)w * kPartialComps * NI + ql;
+        double* P = a.partials + (size_t)w * TC * NI + ql;
 #pragma unroll
-        for (int c = 0; c < kPartialComps; ++c) P[(size_t)c * NI] = v[c];
+        for (int c = 0; c < TC; ++c) P[(size_t)c * NI] = v[c];
       }
     }
   }

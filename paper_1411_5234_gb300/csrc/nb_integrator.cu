@@ -41,6 +41,24 @@ __device__ __forceinline__ void predict1(const dbl4& p, const dbl4& v, const dbl
   vp.z = v.z + t * (a.z + h * j.z);
 }
 
+// Taylor predictor of the 6th-order scheme (Horner form): x + v t + a t^2/2
+// + j t^3/6 + s t^4/24 + c t^5/120, its velocity and its acceleration
+// a + j t + s t^2/2 + c t^3/6 (the sources' accelerations of the snap term).
+__device__ __forceinline__ void predict6(const dbl4& p, const dbl4& v, const dbl4& a,
+                                         const dbl4& j, const dbl4& sn, const dbl4& cr, double t,
+                                         double3& xp, double3& vp, double3& ap) {
+  const double h = 0.5 * t, t3 = t * (1.0 / 3.0), t4 = 0.25 * t, t5 = 0.2 * t;
+  xp.x = p.x + t * (v.x + h * (a.x + t3 * (j.x + t4 * (sn.x + t5 * cr.x))));
+  xp.y = p.y + t * (v.y + h * (a.y + t3 * (j.y + t4 * (sn.y + t5 * cr.y))));
+  xp.z = p.z + t * (v.z + h * (a.z + t3 * (j.z + t4 * (sn.z + t5 * cr.z))));
+  vp.x = v.x + t * (a.x + h * (j.x + t3 * (sn.x + t4 * cr.x)));
+  vp.y = v.y + t * (a.y + h * (j.y + t3 * (sn.y + t4 * cr.y)));
+  vp.z = v.z + t * (a.z + h * (j.z + t3 * (sn.z + t4 * cr.z)));
+  ap.x = a.x + t * (j.x + h * (sn.x + t3 * cr.x));
+  ap.y = a.y + t * (j.y + h * (sn.y + t3 * cr.y));
+  ap.z = a.z + t * (j.z + h * (sn.z + t3 * cr.z));
+}
+
 template <typename T, typename Op>
 __device__ __forceinline__ T block_reduce(T v, Op op, T* sh, T ident) {
   // blockDim.x a multiple of 32, <= 1024
@@ -162,13 +180,18 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
   }
   int32_t due = 0;
   double3 xp = make_double3(0.0, 0.0, 0.0), vp = make_double3(0.0, 0.0, 0.0);
+  double3 ap = make_double3(0.0, 0.0, 0.0);
   double m = 0.0;
+  const bool o6 = d.order == 6;
   if (p >= 0) {
     const int64_t ti = d.t[p];
     due = (count_due && ti + step_ticks(d.level[p], T) == tn) ? 1 : 0;
     const double tau = zero_tau ? 0.0 : ldexp((double)(tn - ti), -T);
     const dbl4 P = d.pos[p], V = d.vel[p], A = d.acc[p], J = d.jerk[p];
-    predict1(P, V, A, J, tau, xp, vp);
+    if (o6)
+      predict6(P, V, A, J, d.snap[p], d.crackle[p], tau, xp, vp, ap);
+    else
+      predict1(P, V, A, J, tau, xp, vp);
     m = P.w;
   }
   if (count_due) {
@@ -184,6 +207,13 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
       d.src64_pos[s] = dbl4{kDummyPos, kDummyPos, kDummyPos, 0.0};
       d.src64_vel[s] = dbl4{0.0, 0.0, 0.0, 0.0};
     }
+    if (o6) d.src64_acc[s] = dbl4{ap.x, ap.y, ap.z, 0.0};  // pads: zero
+  }
+  if (o6 && write_mix && in) {  // [ax][ay][az] float4 groups of 4 slots
+    float* g = reinterpret_cast<float*>(d.src_acc_mix + (s >> 2) * 3) + (s & 3);
+    g[0] = __double2float_rn(ap.x);
+    g[4] = __double2float_rn(ap.y);
+    g[8] = __double2float_rn(ap.z);
   }
   if (write_mix) build_mixed_tile(d.src_mix, d.tiles, tile, s, in, p >= 0, xp, m, vp, shd);
 }
@@ -340,18 +370,24 @@ __global__ void k_scan_plan(Dev d, int32_t nblk, PlanArgs p) {
 //     first row, and the last CTA of the block (arrival counter) adds the
 //     segment sums in segment order.  GB300 runs FP64 at ~2 lanes per SM per
 //     clock, so the segments spread the additions over many SMs.
+// C partial components per target: 7 (acceleration, jerk, potential) or 10
+// (and snap, for the 6th-order force).
+template <int C>
 __device__ __forceinline__ void write_reduced(const ForceArgs& a, int32_t s, const double* v,
                                               int with_acc) {
   const int64_t row = a.rows ? (int64_t)a.rows[s] : (int64_t)s;
   if (with_acc) {
     if (a.out_acc) for (int c = 0; c < 3; ++c) a.out_acc[row * a.sa + c] = a.G * v[c];
     if (a.out_jerk) for (int c = 0; c < 3; ++c) a.out_jerk[row * a.sj + c] = a.G * v[3 + c];
+    if (C > kPartialComps && a.out_snap)
+      for (int c = 0; c < 3; ++c) a.out_snap[row * a.ss + c] = a.G * v[kPartialComps + c];
   }
   if (a.out_pot) a.out_pot[row * a.sp] = a.G * v[6];
 }
 
-constexpr size_t kWideSmem = sizeof(double) * kPartialComps * kWideRows * 32;
+constexpr size_t kWideSmem = sizeof(double) * kPartialCompsSnap * kWideRows * 32;
 
+template <int C>
 __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
                                                            int with_acc) {
   extern __shared__ double red[];  // [component][row r][lane]
@@ -367,15 +403,15 @@ __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
     const int32_t it = local / NI;
     const int32_t q = local - it * NI;
     const int32_t w0 = a.item_off[k] + it * B;
-    double v[kPartialComps];
+    double v[C];
 #pragma unroll
-    for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
+    for (int c = 0; c < C; ++c) v[c] = 0.0;
     for (int32_t b = 0; b < B; ++b) {
-      const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
+      const double* P = a.partials + (size_t)(w0 + b) * C * NI + q;
 #pragma unroll
-      for (int c = 0; c < kPartialComps; ++c) v[c] += P[(size_t)c * NI];
+      for (int c = 0; c < C; ++c) v[c] += P[(size_t)c * NI];
     }
-    write_reduced(a, s, v, with_acc);
+    write_reduced<C>(a, s, v, with_acc);
   }
   // large splits: (i-tile, row segment, block of 32 targets) units
   const int32_t cbs = NI / 32;
@@ -396,21 +432,21 @@ __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
     const bool valid = local < m_k;
     const int32_t w0 = a.item_off[k] + it * B;
     const int32_t b = g * kWideRows + r;
-    double v[kPartialComps];
+    double v[C];
 #pragma unroll
-    for (int c = 0; c < kPartialComps; ++c) v[c] = 0.0;
+    for (int c = 0; c < C; ++c) v[c] = 0.0;
     if (valid && b < B) {
-      const double* P = a.partials + (size_t)(w0 + b) * kPartialComps * NI + q;
+      const double* P = a.partials + (size_t)(w0 + b) * C * NI + q;
 #pragma unroll
-      for (int c = 0; c < kPartialComps; ++c) v[c] = P[(size_t)c * NI];
+      for (int c = 0; c < C; ++c) v[c] = P[(size_t)c * NI];
     }
 #pragma unroll
-    for (int c = 0; c < kPartialComps; ++c) red[(c * kWideRows + r) * 32 + lane] = v[c];
+    for (int c = 0; c < C; ++c) red[(c * kWideRows + r) * 32 + lane] = v[c];
     __syncthreads();
     for (int o = kWideRows / 2; o > 0; o >>= 1) {
       if (r < o) {
 #pragma unroll
-        for (int c = 0; c < kPartialComps; ++c)
+        for (int c = 0; c < C; ++c)
           red[(c * kWideRows + r) * 32 + lane] += red[(c * kWideRows + r + o) * 32 + lane];
       }
       __syncthreads();
@@ -418,17 +454,17 @@ __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
     if (nseg == 1) {
       if (r == 0 && valid) {
 #pragma unroll
-        for (int c = 0; c < kPartialComps; ++c) v[c] = red[(c * kWideRows) * 32 + lane];
-        write_reduced(a, a.act_off[k] + local, v, with_acc);
+        for (int c = 0; c < C; ++c) v[c] = red[(c * kWideRows) * 32 + lane];
+        write_reduced<C>(a, a.act_off[k] + local, v, with_acc);
       }
     } else {
       // segment sum over the segment's first row (only this CTA reads or
       // writes those columns of that row until the block's last CTA)
       if (r == 0) {
         if (valid) {
-          double* P0 = a.partials + (size_t)(w0 + g * kWideRows) * kPartialComps * NI + q;
+          double* P0 = a.partials + (size_t)(w0 + g * kWideRows) * C * NI + q;
 #pragma unroll
-          for (int c = 0; c < kPartialComps; ++c) P0[(size_t)c * NI] = red[(c * kWideRows) * 32 + lane];
+          for (int c = 0; c < C; ++c) P0[(size_t)c * NI] = red[(c * kWideRows) * 32 + lane];
         }
         __threadfence();
       }
@@ -437,9 +473,9 @@ __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
       if (threadIdx.x == 0) last_sh = atomicAdd(cnt, 1) == nseg - 1;
       __syncthreads();
       if (last_sh) {
-        // warp r < kPartialComps adds component r of the segment sums in
+        // warp r < C adds component r of the segment sums in
         // segment order, eight loads in flight at a time
-        if (r < kPartialComps) {
+        if (r < C) {
           __threadfence();
           double acc = 0.0;
           for (int32_t h0 = 0; h0 < nseg; h0 += 8) {
@@ -447,7 +483,7 @@ __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const double* P0 =
-                  a.partials + (size_t)(w0 + (h0 + j) * kWideRows) * kPartialComps * NI + q;
+                  a.partials + (size_t)(w0 + (h0 + j) * kWideRows) * C * NI + q;
               x[j] = (valid && h0 + j < nseg) ? __ldcg(P0 + (size_t)r * NI) : 0.0;
             }
 #pragma unroll
@@ -460,8 +496,8 @@ __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
         if (r == 0) {
           if (valid) {
 #pragma unroll
-            for (int c = 0; c < kPartialComps; ++c) v[c] = red[c * 32 + lane];
-            write_reduced(a, a.act_off[k] + local, v, with_acc);
+            for (int c = 0; c < C; ++c) v[c] = red[c * 32 + lane];
+            write_reduced<C>(a, a.act_off[k] + local, v, with_acc);
           }
           if (lane == 0) *cnt = 0;  // ready for the next launch
         }
@@ -597,6 +633,85 @@ __global__ void k_correct(Dev d, CorrectArgs c) {
       d.t[i] = tn;
       d.level[i] = L;
     }
+  }
+}
+
+// 6th-order Hermite corrector (Sec. 2 item 1, the order of the paper's
+// template code) of the listed particles, one thread per particle.  Over the
+// step t from (x0, v0, a0, j0, s0) to the force (a1, j1, s1) at the predicted
+// end, the quintic through (a0, j0, s0) and (a1, j1, s1) integrates to
+//   v1 = v0 + t/2 (a0 + a1) - t^2/10 (j1 - j0) + t^3/120 (s0 + s1),
+//   x1 = x0 + t/2 (v0 + v1) - t^2/10 (a1 - a0) + t^3/120 (j0 + j1),
+// and its derivatives at the end (D = a1 - a0) are
+//   crackle t^3 = 60 D - t (24 j0 + 36 j1) - t^2 (3 s0 - 9 s1),
+//   pop t^4     = 360 D - t (168 j0 + 192 j1) - t^2 (24 s0 - 36 s1),
+//   a5 t^5      = 720 D - 360 t (j0 + j1) - 60 t^2 (s0 - s1).
+// The step criterion is the generalised Aarseth form of the p-th order
+// Hermite schemes at p = 6, dt = eta (A1 / A4)^(1/3) with
+// A_k = sqrt(|a^(k-1)| |a^(k+1)|) + |a^(k)| over a, j, s, crackle, pop, a5 at
+// the end of the step; the power-of-two level follows the 4th-order rules.
+// The crackle is kept for the next prediction.
+__global__ void k_correct6(Dev d, CorrectArgs c) {
+  const int64_t m = c.count_dev ? (int64_t)*c.count_dev : c.count_host;
+  if (c.reset_tmin && blockIdx.x == 0)  // the block step's t_min is used up
+    for (int32_t k = threadIdx.x; k < d.K; k += blockDim.x) d.t_min[k] = LLONG_MAX;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < m;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = c.active[s];
+    if (i < 0 || i >= d.N) {
+      atomicOr(d.status, kStatusInval);
+      continue;
+    }
+    const int32_t cl = d.cid[i];
+    const int64_t tn = c.t_tgt ? c.t_tgt[cl] : c.t_fixed;
+    const int64_t ti = d.t[i];
+    if (tn <= ti) {  // a step must move forward in time
+      atomicOr(d.status, kStatusInval);
+      continue;
+    }
+    const double t = ldexp((double)(tn - ti), -c.T);
+    int te;
+    const bool pow2 = frexp(t, &te) == 0.5;
+    const double it = pow2 ? ldexp(1.0, 1 - te) : 1.0 / t;  // exact for a block step
+    const double t2 = t * t, t3 = t2 * t, it2 = it * it, it3 = it2 * it;
+    const double h = 0.5 * t, c10 = t2 * 0.1, c120 = t3 * (1.0 / 120.0);
+    const dbl4 X0 = d.pos[i], V0 = d.vel[i], A0 = d.acc[i], J0 = d.jerk[i], S0 = d.snap[i];
+    const double x0[3] = {X0.x, X0.y, X0.z}, v0[3] = {V0.x, V0.y, V0.z};
+    const double a0[3] = {A0.x, A0.y, A0.z}, j0[3] = {J0.x, J0.y, J0.z};
+    const double s0[3] = {S0.x, S0.y, S0.z};
+    double a1[3], j1[3], s1[3], x1[3], v1[3], cr[3], po[3], a5[3];
+    bool finite = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      a1[q] = c.acc[s * c.sa + q];
+      j1[q] = c.jerk[s * c.sj + q];
+      s1[q] = c.snap[s * c.ss + q];
+      v1[q] = v0[q] + h * (a0[q] + a1[q]) - c10 * (j1[q] - j0[q]) + c120 * (s0[q] + s1[q]);
+      x1[q] = x0[q] + h * (v0[q] + v1[q]) - c10 * (a1[q] - a0[q]) + c120 * (j0[q] + j1[q]);
+      const double D = a1[q] - a0[q];
+      cr[q] = (60.0 * D - t * (24.0 * j0[q] + 36.0 * j1[q]) - t2 * (3.0 * s0[q] - 9.0 * s1[q])) *
+              it3;
+      po[q] = (360.0 * D - t * (168.0 * j0[q] + 192.0 * j1[q]) -
+               t2 * (24.0 * s0[q] - 36.0 * s1[q])) * (it3 * it);
+      a5[q] = (720.0 * D - 360.0 * t * (j0[q] + j1[q]) - 60.0 * t2 * (s0[q] - s1[q])) *
+              (it3 * it2);
+      finite = finite && isfinite(x1[q]) && isfinite(v1[q]);
+    }
+    const double na = norm3(a1[0], a1[1], a1[2]), nj = norm3(j1[0], j1[1], j1[2]);
+    const double ns = norm3(s1[0], s1[1], s1[2]), nc = norm3(cr[0], cr[1], cr[2]);
+    const double np = norm3(po[0], po[1], po[2]), nq = norm3(a5[0], a5[1], a5[2]);
+    const double A1 = sqrt(na * ns) + nj, A4 = sqrt(nc * nq) + np;
+    const double dt = A4 > 0.0 ? c.eta * cbrt(A1 / A4) : CUDART_INF;
+    const int32_t L = new_level(dt, d.level[i], tn, c.T, c.lmin, c.lmax);
+    if (!finite) atomicOr(d.status, kStatusNonFinite);
+    d.pos[i] = dbl4{x1[0], x1[1], x1[2], X0.w};
+    d.vel[i] = dbl4{v1[0], v1[1], v1[2], 0.0};
+    d.acc[i] = dbl4{a1[0], a1[1], a1[2], c.pot ? c.pot[s * c.sp] : A0.w};
+    d.jerk[i] = dbl4{j1[0], j1[1], j1[2], 0.0};
+    d.snap[i] = dbl4{s1[0], s1[1], s1[2], 0.0};
+    d.crackle[i] = dbl4{cr[0], cr[1], cr[2], 0.0};
+    d.t[i] = tn;
+    d.level[i] = L;
   }
 }
 
@@ -843,20 +958,36 @@ cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
 }
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
                           int grid, cudaStream_t st) {
-  // one persistent CTA of 1024 threads per SM (its 57 KB of shared memory
+  // one persistent CTA of 1024 threads per SM (its 82 KB of shared memory
   // serve the large splits); exits at once when the plan split nothing
   (void)m_bound;
-  k_reduce<<<grid > 0 ? grid : 1, 32 * kWideRows, kWideSmem, st>>>(a, NI, with_acc ? 1 : 0);
+  const int g = grid > 0 ? grid : 1;
+  if (a.comps == kPartialCompsSnap)
+    k_reduce<kPartialCompsSnap><<<g, 32 * kWideRows, kWideSmem, st>>>(a, NI, with_acc ? 1 : 0);
+  else
+    k_reduce<kPartialComps><<<g, 32 * kWideRows, kWideSmem, st>>>(a, NI, with_acc ? 1 : 0);
   return cudaGetLastError();
 }
 cudaError_t integrator_setup() {
-  return cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_reduce<kPartialComps>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kWideSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_reduce<kPartialCompsSnap>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(kWideSmem));
 }
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {
   // 4 lanes per particle in 32-thread CTAs: a few hundred active particles
   // still spread over many SMs (FP64 arithmetic, ~2 lanes per SM per clock)
   k_correct<<<blocks_for(4 * m_bound, 32), 32, 0, st>>>(d, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_correct6(const Dev& d, const CorrectArgs& c, int64_t m_bound,
+                            cudaStream_t st) {
+  // one thread per particle in 32-thread CTAs: few active particles still
+  // spread over many SMs (FP64 arithmetic)
+  k_correct6<<<blocks_for(m_bound, 32), 32, 0, st>>>(d, c);
   return cudaGetLastError();
 }
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,

@@ -122,6 +122,7 @@ struct CorrectArgs {
   const double* acc; int sa;
   const double* jerk; int sj;
   const double* pot; int sp;  // nullptr: keep the stored potential
+  const double* snap; int ss; // 6th order: the new snap (m rows)
   const int64_t* t_tgt;       // per-cluster target time or nullptr
   int64_t t_fixed;
   double eta;
@@ -151,6 +152,8 @@ cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_b
 // one-time kernel attributes (the reduction's dynamic shared memory)
 cudaError_t integrator_setup();
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st);
+// 6th-order Hermite corrector, step criterion and level of the listed particles
+cudaError_t launch_correct6(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st);
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,
                                cudaStream_t st);
 // caller list -> d.active (slot order), d.rows (caller rows), act_off

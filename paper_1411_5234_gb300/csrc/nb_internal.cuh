@@ -28,6 +28,7 @@ namespace nb {
 
 constexpr int kMaxTickExp = 60;
 constexpr int kPartialComps = 7;     // ax ay az jx jy jz pot
+constexpr int kPartialCompsSnap = 10; // ... and sx sy sz (the 6th-order force)
 constexpr double kDummyPos = 1.0e18; // where massless pad sources sit
 
 // Mixed-precision force kernel shape.
@@ -83,6 +84,14 @@ struct Dev {
                                            // [2] warp-tiles [3] near warp-tiles
   int64_t* t_end = nullptr;      // 1
   int32_t* work_ctr = nullptr;   // next work item of the force kernels (zeroed by the plan)
+  // 6th-order Hermite (order == 6; null otherwise): snap and crackle per
+  // particle (dbl4, w unused), the new snap per active slot, and the
+  // predicted accelerations of the sources (mixed: groups of 4 slots, 3 float4
+  // per group [ax][ay][az]; FP64: dbl4 per slot)
+  int32_t order = 4;
+  dbl4 *snap = nullptr, *crackle = nullptr, *snap_new = nullptr;
+  float4* src_acc_mix = nullptr;
+  dbl4* src64_acc = nullptr;
 };
 
 // Targets, sources and outputs of one force launch.
@@ -111,6 +120,12 @@ struct ForceArgs {
   double eps2;
   uint32_t* status;
   int32_t* work_ctr;        // next work item (zeroed by the plan; nullptr: a fixed share per CTA)
+  // force with snap (the 6th-order scheme): the sources' predicted
+  // accelerations (mixed: float4 groups [ax][ay][az] of 4 slots; FP64: dbl4
+  // per slot), the snap output (nullptr: no snap) and its row stride
+  const void* src_c;
+  double* out_snap; int ss;
+  int comps;                // partial-sum components per target: 7, or 10 with snap
 };
 
 // ---------------------------------------------------------------- helpers
@@ -297,6 +312,10 @@ int force_mixed_ctas_per_sm(int variant);
 cudaError_t launch_force_mixed_acc(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st);
 int force_mixed_acc_ni();
 int force_mixed_acc_ctas_per_sm();
+// acceleration, jerk and snap (the 6th-order force): one mixed shape
+cudaError_t launch_force_mixed_snap(const ForceArgs& a, int grid, bool with_pot, cudaStream_t st);
+int force_mixed_snap_ni();
+int force_mixed_snap_ctas_per_sm();
 // the 64 x 4 shape (force_mixed_ni(2) targets per item) with another
 // separation mode: 1 double-single everywhere, 2 plain FP32
 cudaError_t launch_force_mixed_sep(const ForceArgs& a, int grid, bool with_pot, int sep,
@@ -306,6 +325,6 @@ int force_fp64_ctas_per_sm();
 size_t force_mixed_smem();
 size_t force_fp64_smem();
 
-enum { kF64Full = 0, kF64PotOnly = 1 };
+enum { kF64Full = 0, kF64PotOnly = 1, kF64Snap = 2 };
 
 }  // namespace nb

@@ -27,7 +27,8 @@ FUNCTIONS = [
     "nb_set_state", "nb_stats", "nb_status", "nb_clear_status", "nb_strerror",
     "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
     "nb_energies", "nb_autotune", "nb_step_leapfrog", "nb_check_wait_timeout",
-    "nb_noalloc_status", "nb_measure_rate",
+    "nb_noalloc_status", "nb_measure_rate", "nb_force_snap", "nb_correct_snap",
+    "nb_get_derivs", "nb_set_derivs",
 ]
 
 
@@ -37,7 +38,7 @@ class NbConfig(ctypes.Structure):
                 ("level_max", ctypes.c_int32), ("tick_exp", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("bfactor", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("sort_sources", ctypes.c_int32),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("order", ctypes.c_int32)]
 
 
 class NBError(RuntimeError):
@@ -85,6 +86,10 @@ def _load() -> ctypes.CDLL:
                                             ctypes.c_double, i32, P, P, P, P]),
         "nb_noalloc_status": (ctypes.c_int, [P]),
         "nb_measure_rate": (ctypes.c_int, [P, i32, P]),
+        "nb_force_snap": (ctypes.c_int, [P, P, i64, P, P, P, P]),
+        "nb_correct_snap": (ctypes.c_int, [P, i64, P, i64, P, P, P]),
+        "nb_get_derivs": (ctypes.c_int, [P, P, P]),
+        "nb_set_derivs": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +228,37 @@ class Sim:
                "nb_force")
         self._order_outputs(acc, jerk, pot)
         return acc, jerk, pot
+
+    def force_snap(self, active: torch.Tensor, want_pot: bool = True):
+        """Acceleration, jerk, snap (and potential) of ``active`` from the last
+        prediction (order-6 contexts: nb_force_snap)."""
+        if active.dtype != torch.int32 or not active.is_cuda or not active.is_contiguous():
+            raise ValueError("active must be a contiguous int32 CUDA tensor")
+        m = active.numel()
+        acc, jerk, snap = (torch.empty((m, 3), dtype=torch.float64, device="cuda")
+                           for _ in range(3))
+        pot = torch.empty(m, dtype=torch.float64, device="cuda") if want_pot else None
+        self._order_inputs(active, acc, jerk, snap, pot)
+        _check(lib.nb_force_snap(self._ctx, _dptr(active), m, _dptr(acc), _dptr(jerk),
+                                 _dptr(snap), _dptr(pot)), "nb_force_snap")
+        self._order_outputs(acc, jerk, snap, pot)
+        return acc, jerk, snap, pot
+
+    def correct_snap(self, t_ticks: int, active: torch.Tensor, acc, jerk, snap):
+        self._order_inputs(active, acc, jerk, snap)
+        _check(lib.nb_correct_snap(self._ctx, int(t_ticks), _dptr(active), active.numel(),
+                                   _dptr(acc), _dptr(jerk), _dptr(snap)), "nb_correct_snap")
+
+    def get_derivs(self):
+        """(snap, crackle) of an order-6 context, each (n, 3)."""
+        snap, crackle = np.empty((self.n, 3)), np.empty((self.n, 3))
+        _check(lib.nb_get_derivs(self._ctx, _hptr(snap), _hptr(crackle)), "nb_get_derivs")
+        return snap, crackle
+
+    def set_derivs(self, snap, crackle):
+        snap = np.ascontiguousarray(snap, dtype=np.float64).reshape(self.n, 3)
+        crackle = np.ascontiguousarray(crackle, dtype=np.float64).reshape(self.n, 3)
+        _check(lib.nb_set_derivs(self._ctx, _hptr(snap), _hptr(crackle)), "nb_set_derivs")
 
     def correct(self, t_ticks: int, active: torch.Tensor, acc: torch.Tensor, jerk: torch.Tensor):
         self._order_inputs(active, acc, jerk)

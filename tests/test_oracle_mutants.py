@@ -50,7 +50,11 @@ MUTANTS = {
     "snap_target_acceleration_dropped": ("u[c] = acc_src[3 * j + c] - acc_src[3 * i + c];", "u[c] = acc_src[3 * j + c];"),
     "hermite6_corrector_h2_coefficient": ("- t2 / 10.0 * (j1[i] - j0[i])", "- t2 / 12.0 * (j1[i] - j0[i])"),
     "hermite6_crackle_coefficient": ("crackle[i] = (60.0 * D", "crackle[i] = (30.0 * D"),
-    "hermite6_predictor_crackle_dropped": ("+ s[i] * t4 / 24.0 + c[i] * t5 / 120.0;", "+ s[i] * t4 / 24.0;"),
+    "hermite6_predictor_crackle_dropped": ("+ s[i] * h4 / 24.0 + c[i] * h5 / 120.0;", "+ s[i] * h4 / 24.0;"),
+    "hermite6_predictor_acc_crackle_coefficient": ("ap[i] = a[i] + j[i] * h + s[i] * h2 / 2.0 + c[i] * h3 / 6.0;",
+                                                   "ap[i] = a[i] + j[i] * h + s[i] * h2 / 2.0 + c[i] * h3 / 2.0;"),
+    "hermite6_predictor_velocity_snap_dropped": ("vp[i] = v[i] + a[i] * h + j[i] * h2 / 2.0 + s[i] * h3 / 6.0",
+                                                 "vp[i] = v[i] + a[i] * h + j[i] * h2 / 2.0"),
     "hermite6_dt_exponent": ("return eta * cbrt(A1 / A4);", "return eta * sqrt(A1 / A4);"),
     "leapfrog_drift_before_kick": ("""        oracle_kick(n, vel, acc, h);
         oracle_drift(n, pos, vel, dt);""", """        oracle_drift(n, pos, vel, dt);

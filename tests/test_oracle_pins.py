@@ -534,6 +534,30 @@ def test_hermite6_corrector_exact_for_polynomials():
     assert np.allclose(q1[0], 0.0, atol=1e-8)    # the 7th derivative of x is zero
 
 
+def test_hermite6_predictor_exact_for_quintic_motion():
+    # x(t) = sum_{k<=5} P_k t^k: the 6th-order predictor's Taylor series in
+    # (x, v, a, jerk, snap, crackle) is exact for it, and so are its velocity
+    # and acceleration (to rounding)
+    rng = np.random.default_rng(12)
+    P = rng.normal(size=(6, 3))
+    def deriv(t, d):
+        out = np.zeros(3)
+        for k in range(d, 6):
+            out += P[k] * math.factorial(k) / math.factorial(k - d) * t ** (k - d)
+        return out
+    h = 0.43
+    xp, vp, ap = oracle.hermite6_predict(h, *[deriv(0, d) for d in range(6)])
+    assert np.allclose(xp[0], deriv(h, 0), rtol=1e-14, atol=1e-14)
+    assert np.allclose(vp[0], deriv(h, 1), rtol=1e-14, atol=1e-14)
+    assert np.allclose(ap[0], deriv(h, 2), rtol=1e-14, atol=1e-14)
+    # several particles with their own steps
+    hs = np.array([0.1, 0.25, 0.5])
+    xs, vs, as_ = oracle.hermite6_predict(hs, *[np.array([deriv(0, d)] * 3) for d in range(6)])
+    for k, hk in enumerate(hs):
+        assert np.allclose(xs[k], deriv(hk, 0), rtol=1e-14, atol=1e-14)
+        assert np.allclose(as_[k], deriv(hk, 2), rtol=1e-14, atol=1e-14)
+
+
 def test_hermite6_sixth_order_kepler():
     # closed-form Kepler orbit (e = 0.5, one period), shared steps: halving
     # dt cuts the error by ~2^6
