@@ -96,9 +96,15 @@ def parse():
     return p.parse_args()
 
 
-def integrate(sim, t_end, chunk=512, max_seconds=None):
+def integrate(sim, t_end, chunk=512, max_seconds=None, near=None, resort_factor=None):
     """Block steps until every cluster reaches t_end, or until max_seconds of
-    wall time have passed; returns (device seconds, steps, time reached)."""
+    wall time have passed; returns (device seconds, steps, time reached).
+
+    With a list ``near``, the share of near (target warp, cell) pairs of the
+    mixed kernel over every chunk of steps is appended to it; with
+    ``resort_factor`` the sources are re-sorted (inside the timed run) when a
+    chunk's share exceeds that factor times the share of the first chunk
+    after the last sort (and 2 %); ``near`` then ends with the re-sort count."""
     import torch
     sim.set_end_time(sim.ticks(t_end))
     target = sim.ticks(t_end)
@@ -106,14 +112,29 @@ def integrate(sim, t_end, chunk=512, max_seconds=None):
     ev0.record(sim.stream)
     steps = 0
     t_wall = time.perf_counter()
+    wt0, nt0 = sim.tile_stats() if near is not None else (0, 0)
+    base, resorts = None, 0
     while True:
         sim.step(chunk)
         steps += chunk
         st = sim.stats()
+        if near is not None:
+            wt, nt = sim.tile_stats()
+            share = (nt - nt0) / max(wt - wt0, 1)
+            near.append(share)
+            wt0, nt0 = wt, nt
+            if base is None:
+                base = share
+            elif resort_factor is not None and share > max(resort_factor * base, 0.02):
+                sim.resort_sources()
+                resorts += 1
+                base = None
         if st.t_min >= target:
             break
         if max_seconds is not None and time.perf_counter() - t_wall > max_seconds:
             break
+    if near is not None and resort_factor is not None:
+        near.append(resorts)
     ev1.record(sim.stream)
     ev1.synchronize()
     return ev0.elapsed_time(ev1) * 1e-3, steps, sim.time(st.t_min)
@@ -189,8 +210,11 @@ def workload_drift(args):
                         level_max=lmax, graph_steps=16)
         if prec == nbody.NB_MIXED and not args.no_tune:
             sim.autotune()
+        mixed = prec == nbody.NB_MIXED
+        near = [] if mixed else None
         e0 = sum(sim.energy())
-        secs, _, t_reached = integrate(sim, t_end, max_seconds=args.max_seconds)
+        secs, _, t_reached = integrate(sim, t_end, max_seconds=args.max_seconds, near=near,
+                                       resort_factor=1.5 if mixed else None)
         e1 = sum(sim.energy())
         st = sim.stats()
         assert sim.status() == nbody.NB_OK
@@ -198,7 +222,31 @@ def workload_drift(args):
                      "t_reached": t_reached, "interactions": st.interactions,
                      "block_steps": st.block_steps, "seconds": secs,
                      "interactions_per_s": st.interactions / secs}
+        if mixed:
+            shares = near[:-1]
+            out[name]["near_share"] = {"first_chunk": shares[0], "last_chunk": shares[-1],
+                                       "max": max(shares), "chunks": len(shares),
+                                       "resorts": near[-1],
+                                       "rule": "re-sort when a chunk of 512 steps exceeds "
+                                               "1.5x the first chunk after the last sort"}
         sim.close()
+        if mixed and name == "mixed":
+            # the force kernel's share of the device time: direct launches
+            # with events over the first 1/8 time unit
+            sim = nbody.Sim(c.pos, c.vel, c.mass, eps=eps, precision=prec, level_min=3,
+                            level_max=lmax, graph_steps=0)
+            if not args.no_tune:
+                sim.autotune()
+            sim.profile(True)
+            secs2, _, _ = integrate(sim, min(t_end, 0.125), max_seconds=args.max_seconds)
+            fms, nlaunch = sim.profile_read()
+            assert sim.status() == nbody.NB_OK
+            nsteps = sim.stats().block_steps
+            out[name]["force_kernel_share"] = {
+                "share": fms * 1e-3 / secs2, "t_end": min(t_end, 0.125),
+                "block_steps": nsteps, "force_launches": nlaunch,
+                "us_per_step": secs2 / max(nsteps, 1) * 1e6}
+            sim.close()
     base = out.get("fp64", {}).get("energy_drift")
     comp = out.get("mixed_at_fp64_n", out["mixed"])["energy_drift"]
     if base:

@@ -168,6 +168,72 @@ int nb_force(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
 int nb_force_snap(nb_ctx *ctx, const int32_t *active_idx, int64_t m, double *acc,
                   double *jerk, double *snap, double *pot);
 
+/* ---- j-partition of the force sum (Sec. 2.1: the template code spreads
+ * its force work over many GPUs, MPI between the processes).  The force on a
+ * target is a sum over sources (Eq. 1), so P processes that each hold the
+ * whole particle set can each sum over one piece of the sources and add the
+ * partial results (an all-reduce); each then corrects the same particles
+ * from the same sums, and the replicated states stay identical. */
+
+/* Slot range [*slot_begin, *slot_end) of piece `part` (0 <= part < n_parts)
+ * of a cluster with n_slots source slots: contiguous pieces of
+ * ceil(n_slots / n_parts) slots rounded up to NB_PIECE_ALIGN, so every piece
+ * starts on a tile of the force kernels; together they cover [0, n_slots)
+ * once, and the last ones may be empty.  Host arithmetic only (no context,
+ * no device).  NB_EINVAL for a bad argument. */
+int nb_source_piece(int64_t n_slots, int32_t part, int32_t n_parts, int64_t *slot_begin,
+                    int64_t *slot_end);
+#define NB_PIECE_ALIGN 128
+
+/* The context's source order: *n_slots, the number of source slots (each
+ * cluster's particles padded to a multiple of 4 slots, in the spatial order
+ * nb_init or nb_resort_sources chose); particle_of_slot (host, n_slots
+ * entries, or NULL): the particle held by each slot, -1 for a padding slot;
+ * slot_offsets (host, n_clusters + 1 entries, or NULL): each cluster's first
+ * slot.  A piece of cluster k (nb_source_piece over its slot count) covers
+ * the slots slot_offsets[k] + [begin, end).  Host data only; does not
+ * synchronise. */
+int nb_source_order(nb_ctx *ctx, int64_t *n_slots, int32_t *particle_of_slot,
+                    int64_t *slot_offsets);
+
+/* nb_force restricted to the sources in piece `part` of `n_parts` of every
+ * cluster's source order (nb_source_piece): the partial acceleration, jerk
+ * and potential, whose sum over part = 0 .. n_parts-1 is nb_force's result
+ * up to rounding.  n_parts == 1 is nb_force itself.  The targets, outputs,
+ * asynchrony and errors are nb_force's; NB_EINVAL for a bad part. */
+int nb_force_range(nb_ctx *ctx, const int32_t *active_idx, int64_t m, int32_t part,
+                   int32_t n_parts, double *acc, double *jerk, double *pot);
+
+/* One block step (nb_step_block, Sec. 2 item 2) split around the sum of its
+ * force over processes.  nb_block_force takes the next block time, predicts,
+ * lists the active set and evaluates its force from piece `part` of
+ * `n_parts` of the sources, then waits and reports *m_out, the number of
+ * active particles, and the device addresses of the step's force rows:
+ * *acc_rows, *jerk_rows and, in an order-6 context, *snap_rows (NULL in
+ * order 4), each m rows of 4 doubles (x, y, z, and one unused double), row k
+ * for the k-th particle of the step's active list.  These rows belong to the
+ * context's workspace; the caller may add the other processes' partial rows
+ * into them in place (an all-reduce over the first 4 m doubles of each), on
+ * the context's stream or after it.  nb_block_correct then applies the
+ * corrector of Sec. 2 item 1 (nb_correct, or nb_correct_snap in order 6) to
+ * those rows and closes the step.  NB_ESTATE: nb_block_force while a step is
+ * open, nb_block_correct with none open, or nb_step_block while one is open.
+ * Output pointers other than m_out may be NULL. */
+int nb_block_force(nb_ctx *ctx, int32_t part, int32_t n_parts, int64_t *m_out,
+                   double **acc_rows, double **jerk_rows, double **snap_rows);
+int nb_block_correct(nb_ctx *ctx);
+
+/* Re-sort every cluster's source slots along the Hilbert curve of the
+ * particles' current positions.  nb_init orders the slots by the initial
+ * positions; as the particles move, the cells of consecutive slots spread
+ * out and more (target warp, cell) pairs take the mixed kernel's near path
+ * (the double-single separations of Sec. 2 item 4), which is slower.  The
+ * sources are then predicted to each cluster's current block time (call
+ * nb_predict again before nb_force at another time).  Later force results
+ * change by rounding only (the summation follows the slot order).
+ * Synchronises; NB_ESTATE while a split block step is open. */
+int nb_resort_sources(nb_ctx *ctx);
+
 /* Hermite correction (Sec. 2 item 1) of the m particles in active_idx
  * (device, as for nb_force) from their own times to t_ticks, given their new
  * acceleration and jerk evaluated at the predicted state (device m x 3, as

@@ -218,6 +218,11 @@ struct nb_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   double prof_ms = 0.0;
   int64_t prof_launches = 0;
+  // j-partition: the piece of every cluster's sources the force launches of
+  // the current call sum over (parts <= 1: all sources; set by PieceScope)
+  int32_t part = 0, parts = 1;
+  // a block step split by nb_block_force, waiting for nb_block_correct
+  bool block_open = false;
 };
 
 namespace {
@@ -227,6 +232,8 @@ namespace {
     cudaError_t e_ = (x);                      \
     if (e_ != cudaSuccess) return NB_ECUDA;    \
   } while (0)
+
+static_assert(kSrcPieceAlign == NB_PIECE_ALIGN, "piece alignment of the ABI");
 
 // every mode but FP64 uses the mixed source layout and kernel family
 bool is_mixed(const nb_ctx* c) { return c->cfg.precision != NB_FP64; }
@@ -274,8 +281,24 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, doub
   a.out_snap = nullptr;
   a.ss = 0;
   a.comps = kPartialComps;
+  a.part = c->part;
+  a.parts = c->parts;
   return a;
 }
+
+// The force launches enqueued while a PieceScope lives sum over piece `part`
+// of `parts` of each cluster's sources.
+struct PieceScope {
+  nb_ctx* c;
+  PieceScope(nb_ctx* c_, int32_t part, int32_t parts) : c(c_) {
+    c->part = part;
+    c->parts = parts;
+  }
+  ~PieceScope() {
+    c->part = 0;
+    c->parts = 1;
+  }
+};
 
 PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count, bool acc_only = false,
                    bool snap = false) {
@@ -289,6 +312,8 @@ PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count, bool acc_only 
   p.part_items = c->L.part_items;
   p.step_mode = step_mode;
   p.count = count;
+  p.part = c->part;
+  p.parts = c->parts;
   return p;
 }
 
@@ -415,7 +440,10 @@ cudaError_t enqueue_force_snap(nb_ctx* c, const int32_t* active, const int32_t* 
   return launch_reduce(fa, ni, true, m_bound, c->sms, c->st);
 }
 
-cudaError_t enqueue_block_step(nb_ctx* c) {
+// First half of a block step: the next block time, the prediction, the
+// active list and its force (rows of 4 doubles in acc_new, jerk_new and, in
+// the 6th-order scheme, snap_new, in active-list order).
+cudaError_t enqueue_block_force(nb_ctx* c) {
   const int T = c->cfg.tick_exp;
   const bool f64 = !is_mixed(c);
   cudaError_t e = launch_tmin(c->d, T, c->st);
@@ -429,48 +457,42 @@ cudaError_t enqueue_block_step(nb_ctx* c) {
   double* jn = reinterpret_cast<double*>(c->d.jerk_new);
   if (o6) {
     double* sn = reinterpret_cast<double*>(c->d.snap_new);
-    e = enqueue_force_snap(c, c->d.active, nullptr, an, 4, jn, 4, sn, 4, nullptr, 0, 1, 1,
-                           c->d.N, true);
-    if (e != cudaSuccess) return e;
-    CorrectArgs ca{};
-    ca.active = c->d.active;
-    ca.count_dev = c->d.act_off + c->d.K;
-    ca.acc = an;
-    ca.sa = 4;
-    ca.jerk = jn;
-    ca.sj = 4;
-    ca.snap = sn;
-    ca.ss = 4;
-    ca.pot = nullptr;
-    ca.sp = 0;
-    ca.t_tgt = c->d.t_cur;
-    ca.eta = c->cfg.eta;
-    ca.T = T;
-    ca.lmin = c->cfg.level_min;
-    ca.lmax = c->cfg.level_max;
-    ca.reset_tmin = 1;
-    return launch_correct6(c->d, ca, c->d.N, c->st);
+    return enqueue_force_snap(c, c->d.active, nullptr, an, 4, jn, 4, sn, 4, nullptr, 0, 1, 1,
+                              c->d.N, true);
   }
   // the integrator needs no potential: the force kernel skips it here
-  e = enqueue_force(c, c->d.active, nullptr, an, 4, jn, 4, nullptr, 0, f64, 1, 1, false,
-                    c->d.N, true);
-  if (e != cudaSuccess) return e;
+  return enqueue_force(c, c->d.active, nullptr, an, 4, jn, 4, nullptr, 0, f64, 1, 1, false,
+                       c->d.N, true);
+}
+
+// Second half: the corrector of the step's active list from those rows.
+cudaError_t enqueue_block_correct(nb_ctx* c) {
   CorrectArgs ca{};
   ca.active = c->d.active;
   ca.count_dev = c->d.act_off + c->d.K;
-  ca.acc = an;
+  ca.acc = reinterpret_cast<double*>(c->d.acc_new);
   ca.sa = 4;
-  ca.jerk = jn;
+  ca.jerk = reinterpret_cast<double*>(c->d.jerk_new);
   ca.sj = 4;
   ca.pot = nullptr;
   ca.sp = 0;
   ca.t_tgt = c->d.t_cur;
   ca.eta = c->cfg.eta;
-  ca.T = T;
+  ca.T = c->cfg.tick_exp;
   ca.lmin = c->cfg.level_min;
   ca.lmax = c->cfg.level_max;
   ca.reset_tmin = 1;
+  if (c->cfg.order == 6) {
+    ca.snap = reinterpret_cast<double*>(c->d.snap_new);
+    ca.ss = 4;
+    return launch_correct6(c->d, ca, c->d.N, c->st);
+  }
   return launch_correct(c->d, ca, c->d.N, c->st);
+}
+
+cudaError_t enqueue_block_step(nb_ctx* c) {
+  const cudaError_t e = enqueue_block_force(c);
+  return e != cudaSuccess ? e : enqueue_block_correct(c);
 }
 
 int sync_status(nb_ctx* c) {
@@ -750,6 +772,97 @@ int nb_force_snap(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, 
   return NB_OK;
 }
 
+int nb_source_piece(int64_t n_slots, int32_t part, int32_t n_parts, int64_t* slot_begin,
+                    int64_t* slot_end) {
+  if (n_slots < 0 || n_parts < 1 || part < 0 || part >= n_parts || !slot_begin || !slot_end)
+    return NB_EINVAL;
+  src_piece(n_slots, part, n_parts, slot_begin, slot_end);
+  return NB_OK;
+}
+
+int nb_source_order(nb_ctx* c, int64_t* n_slots, int32_t* particle_of_slot,
+                    int64_t* slot_offsets) {
+  if (!c || !n_slots) return NB_EINVAL;
+  *n_slots = c->d.S;
+  if (particle_of_slot)
+    std::copy(c->sperm_host.begin(), c->sperm_host.end(), particle_of_slot);
+  if (slot_offsets) {
+    slot_offsets[0] = 0;
+    for (int32_t k = 0; k < c->d.K; ++k)
+      slot_offsets[k + 1] =
+          slot_offsets[k] + round_up64(c->off_host[k + 1] - c->off_host[k], 4);
+  }
+  return NB_OK;
+}
+
+int nb_force_range(nb_ctx* c, const int32_t* active_idx, int64_t m, int32_t part,
+                   int32_t n_parts, double* acc, double* jerk, double* pot) {
+  NvtxRange nvtx_range("nb_force_range");
+  if (!c || n_parts < 1 || part < 0 || part >= n_parts) return NB_EINVAL;
+  PieceScope piece(c, part, n_parts);
+  return nb_force(c, active_idx, m, acc, jerk, pot);
+}
+
+int nb_block_force(nb_ctx* c, int32_t part, int32_t n_parts, int64_t* m_out, double** acc_rows,
+                   double** jerk_rows, double** snap_rows) {
+  NvtxRange nvtx_range("nb_block_force");
+  if (!c || !m_out || n_parts < 1 || part < 0 || part >= n_parts) return NB_EINVAL;
+  if (c->block_open) return NB_ESTATE;
+  {
+    PieceScope piece(c, part, n_parts);
+    NB_TRY(enqueue_block_force(c));
+  }
+  int32_t m = 0;
+  NB_TRY(cudaMemcpyAsync(&m, c->d.act_off + c->d.K, sizeof m, cudaMemcpyDeviceToHost, c->st));
+  const int rc = sync_status(c);
+  if (rc != NB_OK) return rc;
+  c->block_open = true;
+  *m_out = m;
+  if (acc_rows) *acc_rows = reinterpret_cast<double*>(c->d.acc_new);
+  if (jerk_rows) *jerk_rows = reinterpret_cast<double*>(c->d.jerk_new);
+  if (snap_rows) *snap_rows = reinterpret_cast<double*>(c->d.snap_new);
+  return NB_OK;
+}
+
+int nb_block_correct(nb_ctx* c) {
+  NvtxRange nvtx_range("nb_block_correct");
+  if (!c) return NB_EINVAL;
+  if (!c->block_open) return NB_ESTATE;
+  c->block_open = false;
+  NB_TRY(enqueue_block_correct(c));
+  return NB_OK;
+}
+
+int nb_resort_sources(nb_ctx* c) {
+  NvtxRange nvtx_range("nb_resort_sources");
+  if (!c) return NB_EINVAL;
+  if (c->block_open) return NB_ESTATE;
+  Dev& d = c->d;
+  const int64_t N = d.N;
+  const int32_t K = d.K;
+  std::vector<double> p4(4 * N), p3(3 * N);
+  NB_TRY(cudaMemcpyAsync(p4.data(), d.pos, 32 * N, cudaMemcpyDeviceToHost, c->st));
+  int rc = sync_status(c);
+  if (rc != NB_OK) return rc;
+  for (int64_t i = 0; i < N; ++i)
+    for (int q = 0; q < 3; ++q) p3[3 * i + q] = p4[4 * i + q];
+  std::vector<int64_t> soff(K + 1, 0);
+  for (int32_t k = 0; k < K; ++k)
+    soff[k + 1] = soff[k] + round_up64(c->off_host[k + 1] - c->off_host[k], 4);
+  std::vector<int32_t> sperm(d.S), sinv(N);
+  source_order(p3.data(), c->off_host.data(), K, soff.data(), c->cfg.sort_sources != 0, sperm,
+               sinv);
+  NB_TRY(cudaMemcpyAsync(d.sperm, sperm.data(), 4 * d.S, cudaMemcpyHostToDevice, c->st));
+  NB_TRY(cudaMemcpyAsync(d.sinv, sinv.data(), 4 * N, cudaMemcpyHostToDevice, c->st));
+  // the sources in the new order, predicted to each cluster's block time
+  const bool f64 = !is_mixed(c);
+  NB_TRY(launch_predict(d, d.t_cur, 0, c->cfg.tick_exp, !f64, f64, false, c->st));
+  rc = sync_status(c);  // the host vectors are released after this
+  if (rc != NB_OK) return rc;
+  c->sperm_host = sperm;
+  return NB_OK;
+}
+
 int nb_correct_snap(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
                     const double* acc, const double* jerk, const double* snap) {
   NvtxRange nvtx_range("nb_correct_snap");
@@ -864,6 +977,7 @@ int nb_step_leapfrog(nb_ctx* c, int64_t n_steps, int64_t dt_ticks) {
 int nb_step_block(nb_ctx* c, int64_t n_steps, int64_t* t_ticks_out, int64_t* m_last_out) {
   NvtxRange nvtx_range("nb_step_block");
   if (!c || n_steps < 0) return NB_EINVAL;
+  if (c->block_open) return NB_ESTATE;
   if (n_steps == 0 && m_last_out) {
     // nothing corrected: clear the count the report below reads
     NB_TRY(cudaMemsetAsync(c->d.act_off + c->d.K, 0, sizeof(int32_t), c->st));

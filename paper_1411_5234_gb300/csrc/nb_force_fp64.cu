@@ -173,9 +173,12 @@ __global__ void __launch_bounds__(NT) k_force_fp64(const ForceArgs a) {
     const int32_t b = l - it * B;
     const int64_t sk0 = a.soff[k];
     const int64_t S_k = a.soff[k + 1] - sk0;
-    const int64_t L = chunk_len(S_k, B, JT);
-    const int64_t j0 = sk0 + b * L;
-    const int64_t j1 = sk0 + min(S_k, (int64_t)(b + 1) * L);
+    // chunk b of B of the cluster's sources, or of this process's piece
+    int64_t pb = 0, pe = S_k;
+    if (a.parts > 1) src_piece(S_k, a.part, a.parts, &pb, &pe);
+    const int64_t L = chunk_len(pe - pb, B, JT);
+    const int64_t j0 = sk0 + pb + b * L;
+    const int64_t j1 = sk0 + pb + min(pe - pb, (int64_t)(b + 1) * L);
     const int32_t a0 = a.act_off[k];
     const int32_t m_k = a.act_off[k + 1] - a0;
     const int64_t p0 = a.off[k], p1 = a.off[k + 1];
@@ -207,8 +210,8 @@ __global__ void __launch_bounds__(NT) k_force_fp64(const ForceArgs a) {
 #pragma unroll
     for (int c = 0; c < 10; ++c) { s.th[c] = 0.0; s.tl[c] = 0.0; }
 
-    const int64_t ntile = ceil_div64(j1 - j0, JT);
-    if (tid == 0) {
+    const int64_t ntile = ceil_div64(j1 - j0, JT);  // 0: an empty piece
+    if (tid == 0 && ntile > 0) {
       issue64<MODE>(sp[0], sv[0], sa[0], &bar[0], gp, gv, ga, j0, min((int64_t)JT, j1 - j0));
       pending[0] = true;
       if (ntile > 1) {

@@ -30,8 +30,6 @@ template <bool POT> using S5 = mixk::MixShape<128, 2, POT, false, false, 2, 2, t
 template <bool POT> using SA = mixk::MixShape<64, 4, POT, false, true, 1, 6, false, mixk::kSepMixed, 4, 2>;
 // acceleration, jerk and snap (the 6th-order Hermite force): 64 x 2
 template <bool POT> using SS = mixk::MixShape<64, 2, POT, false, true, 1, 5, true, mixk::kSepMixed, 4, 1, true>;
-template <bool POT> using SS3 = mixk::MixShape<64, 3, POT, false, true, 1, 4, true, mixk::kSepMixed, 4, 1, true>;
-template <bool POT> using SS4 = mixk::MixShape<64, 2, POT, false, true, 1, 4, true, mixk::kSepMixed, 4, 2, true>;
 // the default shape with double-single separations everywhere, and with plain
 // FP32 separations (NB_DS, NB_FP32: accuracy and speed bounds of the mixed path)
 template <bool POT> using SD = mixk::MixShape<64, 4, POT, false, true, 1, 4, true, mixk::kSepDS, 4, 2>;
@@ -115,8 +113,6 @@ cudaError_t launch_force_mixed_snap(const ForceArgs& a, int grid, bool with_pot,
   if (with_pot) return launch_shape<SS<true>>(a, grid, st);
   return launch_shape<SS<false>>(a, grid, st);
 }
-// (compile checks of other snap shapes)
-int snap_shape_check() { return occupancy<SS3<false>>() + occupancy<SS4<false>>(); }
 
 size_t force_mixed_smem() { return sizeof(float4) * 2 * mixk::kTileF4; }
 

@@ -62,6 +62,8 @@
 // folded into the compensated totals once per stage, so ST = 2 halves the
 // flushes, syncs and waits (FP32 runs of 128 terms per lane instead of 64).
 #pragma once
+#include <type_traits>
+
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -102,9 +104,15 @@ struct Target {
   f2 nvx, nvy, nvz;              // -v_i as broadcast pairs
   f2 ex, ey, ez;                 // hi part of c_J - r_i (broadcast)
   f2 ax, ay, az, jx, jy, jz, pt; // per-stage sums (2 lanes)
-  f2 nax, nay, naz;              // snap shapes: -a_i (the predicted acceleration)
-  f2 sx, sy, sz;                 // snap shapes: per-stage snap sums
 };
+// ... and of a snap shape (kept apart, so that the other shapes compile to
+// the same code as without the snap)
+struct TargetS : Target {
+  f2 nax, nay, naz;              // -a_i (the predicted acceleration, broadcast)
+  f2 sx, sy, sz;                 // per-stage snap sums
+};
+template <class Sh>
+using TargetOf = typename std::conditional<Sh::SNAP, TargetS, Target>::type;
 
 // compensated totals per target: a (3), jerk (3), potential, [snap (3)]
 constexpr int kTotComps = kPartialCompsSnap;
@@ -151,16 +159,12 @@ __device__ __forceinline__ void ds_sub0(float c, float bh, float bl, float& rh, 
   rl = err - (rh - s);
 }
 
-// Shared tail of one pair step: from the separation d, relative velocity w
-// to the accumulators.
-// Snap shapes also take u = a_j - a_i and add the snap term
-// m (u - 6 alpha (w - 3 alpha d) - 3 beta d) / s^3, alpha = d.w / s^2,
-// beta = (w.w + d.u) / s^2 + alpha^2 (the second time derivative of the pair
-// term of Eq. 2; 22 more FP32 lane-ops per interaction).
+// One pair step, from the separation d and relative velocity w to the
+// accumulators: pair_head forms 1/s, m/s^3, the potential and acceleration
+// terms (shared by every shape); pair_tail adds the jerk term.
 template <class Sh, bool MASK>
-__device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx, f2 wy, f2 wz,
-                                          f2 ux, f2 uy, f2 uz, f2 m, f2 eps2, int64_t js,
-                                          int64_t slot) {
+__device__ __forceinline__ void pair_head(Target& s, f2 dx, f2 dy, f2 dz, f2 m, f2 eps2,
+                                          int64_t js, int64_t slot, f2& mr3, f2& r2inv) {
   f2 r2 = f2_fma(dx, dx, eps2);
   r2 = f2_fma(dy, dy, r2);
   r2 = f2_fma(dz, dz, r2);
@@ -173,36 +177,21 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
     rinv = f2_pack(a.x, a.y);
     rr = f2_pack(c.x, c.y);
   }
-  const f2 r2inv = Sh::RCP ? rr : f2_mul(rinv, rinv);
+  r2inv = Sh::RCP ? rr : f2_mul(rinv, rinv);
   const f2 mri = f2_mul(m, rinv);
-  const f2 mr3 = f2_mul(mri, r2inv);
+  mr3 = f2_mul(mri, r2inv);
   if (Sh::POT) s.pt = f2_add(s.pt, mri);
   s.ax = f2_fma(mr3, dx, s.ax);
   s.ay = f2_fma(mr3, dy, s.ay);
   s.az = f2_fma(mr3, dz, s.az);
-  if constexpr (Sh::SNAP) {
-    f2 rv = f2_mul(dx, wx);
-    rv = f2_fma(dy, wy, rv);
-    rv = f2_fma(dz, wz, rv);
-    f2 wdu = f2_mul(wx, wx);  // w.w + d.u
-    wdu = f2_fma(wy, wy, wdu);
-    wdu = f2_fma(wz, wz, wdu);
-    wdu = f2_fma(dx, ux, wdu);
-    wdu = f2_fma(dy, uy, wdu);
-    wdu = f2_fma(dz, uz, wdu);
-    const f2 r2m3 = f2_mul(r2inv, f2_pack(-3.f, -3.f));
-    const f2 t = f2_mul(rv, r2m3);                 // -3 alpha
-    const f2 alpha = f2_mul(rv, r2inv);
-    const f2 c2 = f2_fma(alpha, t, f2_mul(wdu, r2m3));  // -3 beta
-    const f2 c1 = f2_add(t, t);                    // -6 alpha
-    const f2 jx = f2_fma(t, dx, wx), jy = f2_fma(t, dy, wy), jz = f2_fma(t, dz, wz);
-    s.jx = f2_fma(mr3, jx, s.jx);
-    s.jy = f2_fma(mr3, jy, s.jy);
-    s.jz = f2_fma(mr3, jz, s.jz);
-    s.sx = f2_fma(mr3, f2_fma(c2, dx, f2_fma(c1, jx, ux)), s.sx);
-    s.sy = f2_fma(mr3, f2_fma(c2, dy, f2_fma(c1, jy, uy)), s.sy);
-    s.sz = f2_fma(mr3, f2_fma(c2, dz, f2_fma(c1, jz, uz)), s.sz);
-  } else if constexpr (Sh::JERK) {
+}
+
+template <class Sh, bool MASK>
+__device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx, f2 wy, f2 wz,
+                                          f2 m, f2 eps2, int64_t js, int64_t slot) {
+  f2 mr3, r2inv;
+  pair_head<Sh, MASK>(s, dx, dy, dz, m, eps2, js, slot, mr3, r2inv);
+  if constexpr (Sh::JERK) {
     f2 rv = f2_mul(dx, wx);
     rv = f2_fma(dy, wy, rv);
     rv = f2_fma(dz, wz, rv);
@@ -210,8 +199,42 @@ __device__ __forceinline__ void pair_tail(Target& s, f2 dx, f2 dy, f2 dz, f2 wx,
     s.jx = f2_fma(mr3, f2_fma(t, dx, wx), s.jx);
     s.jy = f2_fma(mr3, f2_fma(t, dy, wy), s.jy);
     s.jz = f2_fma(mr3, f2_fma(t, dz, wz), s.jz);
-    (void)ux; (void)uy; (void)uz;
+  } else {
+    (void)wx; (void)wy; (void)wz;
   }
+}
+
+// The snap shapes' tail: also u = a_j - a_i, and the snap term
+// m (u - 6 alpha (w - 3 alpha d) - 3 beta d) / s^3, alpha = d.w / s^2,
+// beta = (w.w + d.u) / s^2 + alpha^2 (the second time derivative of the pair
+// term of Eq. 2; 22 more FP32 lane-ops per interaction).
+template <class Sh, bool MASK>
+__device__ __forceinline__ void pair_tail_snap(TargetS& s, f2 dx, f2 dy, f2 dz, f2 wx, f2 wy,
+                                               f2 wz, f2 ux, f2 uy, f2 uz, f2 m, f2 eps2,
+                                               int64_t js, int64_t slot) {
+  f2 mr3, r2inv;
+  pair_head<Sh, MASK>(s, dx, dy, dz, m, eps2, js, slot, mr3, r2inv);
+  f2 rv = f2_mul(dx, wx);
+  rv = f2_fma(dy, wy, rv);
+  rv = f2_fma(dz, wz, rv);
+  f2 wdu = f2_mul(wx, wx);  // w.w + d.u
+  wdu = f2_fma(wy, wy, wdu);
+  wdu = f2_fma(wz, wz, wdu);
+  wdu = f2_fma(dx, ux, wdu);
+  wdu = f2_fma(dy, uy, wdu);
+  wdu = f2_fma(dz, uz, wdu);
+  const f2 r2m3 = f2_mul(r2inv, f2_pack(-3.f, -3.f));
+  const f2 t = f2_mul(rv, r2m3);                 // -3 alpha
+  const f2 alpha = f2_mul(rv, r2inv);
+  const f2 c2 = f2_fma(alpha, t, f2_mul(wdu, r2m3));  // -3 beta
+  const f2 c1 = f2_add(t, t);                    // -6 alpha
+  const f2 jx = f2_fma(t, dx, wx), jy = f2_fma(t, dy, wy), jz = f2_fma(t, dz, wz);
+  s.jx = f2_fma(mr3, jx, s.jx);
+  s.jy = f2_fma(mr3, jy, s.jy);
+  s.jz = f2_fma(mr3, jz, s.jz);
+  s.sx = f2_fma(mr3, f2_fma(c2, dx, f2_fma(c1, jx, ux)), s.sx);
+  s.sy = f2_fma(mr3, f2_fma(c2, dy, f2_fma(c1, jy, uy)), s.sy);
+  s.sz = f2_fma(mr3, f2_fma(c2, dz, f2_fma(c1, jz, uz)), s.sz);
 }
 
 // Source accelerations of the snap shapes: 3 float4 per group of 4 slots
@@ -224,32 +247,40 @@ constexpr int kAccTileF4 = JT / 4 * kAccGroupF4;
 template <class Sh, int NG = 0>
 __device__ __forceinline__ void tile_far(const float4* __restrict__ tile,
                                          const float4* __restrict__ acc, int ngroups,
-                                         Target (&tg)[Sh::IPT], f2 eps2) {
+                                         TargetOf<Sh> (&tg)[Sh::IPT], f2 eps2) {
   const int n = NG > 0 ? NG : ngroups;
 #pragma unroll Sh::UNR
   for (int g = 0; g < n; ++g) {
     const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
                      vy = G[cVY], vz = G[cVZ];
-    ulonglong2 ax{0ull, 0ull}, ay{0ull, 0ull}, az{0ull, 0ull};
     if constexpr (Sh::SNAP) {
       const ulonglong2* A = reinterpret_cast<const ulonglong2*>(acc + g * kAccGroupF4);
-      ax = A[0];
-      ay = A[1];
-      az = A[2];
-    }
+      const ulonglong2 ax = A[0], ay = A[1], az = A[2];
 #pragma unroll
-    for (int r = 0; r < Sh::IPT; ++r) {
-      Target& s = tg[r];
-      const bool sn = Sh::SNAP;
-      pair_tail<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
-                           f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz),
-                           sn ? f2_add(ax.x, s.nax) : 0ull, sn ? f2_add(ay.x, s.nay) : 0ull,
-                           sn ? f2_add(az.x, s.naz) : 0ull, m.x, eps2, 0, -1);
-      pair_tail<Sh, false>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
-                           f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz),
-                           sn ? f2_add(ax.y, s.nax) : 0ull, sn ? f2_add(ay.y, s.nay) : 0ull,
-                           sn ? f2_add(az.y, s.naz) : 0ull, m.y, eps2, 0, -1);
+      for (int r = 0; r < Sh::IPT; ++r) {
+        TargetS& s = tg[r];
+        pair_tail_snap<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey),
+                                  f2_add(dzh.x, s.ez), f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy),
+                                  f2_add(vz.x, s.nvz), f2_add(ax.x, s.nax), f2_add(ay.x, s.nay),
+                                  f2_add(az.x, s.naz), m.x, eps2, 0, -1);
+        pair_tail_snap<Sh, false>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey),
+                                  f2_add(dzh.y, s.ez), f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy),
+                                  f2_add(vz.y, s.nvz), f2_add(ax.y, s.nax), f2_add(ay.y, s.nay),
+                                  f2_add(az.y, s.naz), m.y, eps2, 0, -1);
+      }
+    } else {
+      (void)acc;
+#pragma unroll
+      for (int r = 0; r < Sh::IPT; ++r) {
+        Target& s = tg[r];
+        pair_tail<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
+                             f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
+                             eps2, 0, -1);
+        pair_tail<Sh, false>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
+                             f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), m.y,
+                             eps2, 0, -1);
+      }
     }
   }
 }
@@ -261,45 +292,47 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ tile,
 template <class Sh, bool MASK>
 __device__ __forceinline__ void tile_near_one(const float4* __restrict__ tile,
                                               const float4* __restrict__ acc, int ngroups,
-                                              int64_t slot0, Target& s, f2 elx, f2 ely, f2 elz,
-                                              int64_t slot, f2 eps2) {
+                                              int64_t slot0, TargetOf<Sh>& s, f2 elx, f2 ely,
+                                              f2 elz, int64_t slot, f2 eps2) {
 #pragma unroll Sh::NU
   for (int g = 0; g < ngroups; ++g) {
     const ulonglong2* G = reinterpret_cast<const ulonglong2*>(tile + g * kGroupF4);
     const ulonglong2 dxh = G[cDXH], dyh = G[cDYH], dzh = G[cDZH], m = G[cM], vx = G[cVX],
                      vy = G[cVY], vz = G[cVZ], dxl = G[cDXL], dyl = G[cDYL], dzl = G[cDZL];
-    f2 ux0 = 0ull, uy0 = 0ull, uz0 = 0ull, ux1 = 0ull, uy1 = 0ull, uz1 = 0ull;
+    const int64_t js = slot0 + 4 * g;
+    f2 dx0, dy0, dz0, dx1, dy1, dz1;
+    if constexpr (Sh::SEP == kSepFP32) {
+      dx0 = f2_add(dxh.x, s.ex);
+      dy0 = f2_add(dyh.x, s.ey);
+      dz0 = f2_add(dzh.x, s.ez);
+      dx1 = f2_add(dxh.y, s.ex);
+      dy1 = f2_add(dyh.y, s.ey);
+      dz1 = f2_add(dzh.y, s.ez);
+      (void)dxl; (void)dyl; (void)dzl; (void)elx; (void)ely; (void)elz;
+    } else {
+      dx0 = f2_add(f2_add(dxh.x, s.ex), f2_add(dxl.x, elx));
+      dy0 = f2_add(f2_add(dyh.x, s.ey), f2_add(dyl.x, ely));
+      dz0 = f2_add(f2_add(dzh.x, s.ez), f2_add(dzl.x, elz));
+      dx1 = f2_add(f2_add(dxh.y, s.ex), f2_add(dxl.y, elx));
+      dy1 = f2_add(f2_add(dyh.y, s.ey), f2_add(dyl.y, ely));
+      dz1 = f2_add(f2_add(dzh.y, s.ez), f2_add(dzl.y, elz));
+    }
     if constexpr (Sh::SNAP) {
       const ulonglong2* A = reinterpret_cast<const ulonglong2*>(acc + g * kAccGroupF4);
       const ulonglong2 ax = A[0], ay = A[1], az = A[2];
-      ux0 = f2_add(ax.x, s.nax);
-      uy0 = f2_add(ay.x, s.nay);
-      uz0 = f2_add(az.x, s.naz);
-      ux1 = f2_add(ax.y, s.nax);
-      uy1 = f2_add(ay.y, s.nay);
-      uz1 = f2_add(az.y, s.naz);
+      pair_tail_snap<Sh, MASK>(s, dx0, dy0, dz0, f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy),
+                               f2_add(vz.x, s.nvz), f2_add(ax.x, s.nax), f2_add(ay.x, s.nay),
+                               f2_add(az.x, s.naz), m.x, eps2, js, slot);
+      pair_tail_snap<Sh, MASK>(s, dx1, dy1, dz1, f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy),
+                               f2_add(vz.y, s.nvz), f2_add(ax.y, s.nax), f2_add(ay.y, s.nay),
+                               f2_add(az.y, s.naz), m.y, eps2, js + 2, slot);
+    } else {
+      (void)acc;
+      pair_tail<Sh, MASK>(s, dx0, dy0, dz0, f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy),
+                          f2_add(vz.x, s.nvz), m.x, eps2, js, slot);
+      pair_tail<Sh, MASK>(s, dx1, dy1, dz1, f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy),
+                          f2_add(vz.y, s.nvz), m.y, eps2, js + 2, slot);
     }
-    const int64_t js = slot0 + 4 * g;
-    if constexpr (Sh::SEP == kSepFP32) {
-      pair_tail<Sh, MASK>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
-                          f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), ux0,
-                          uy0, uz0, m.x, eps2, js, slot);
-      pair_tail<Sh, MASK>(s, f2_add(dxh.y, s.ex), f2_add(dyh.y, s.ey), f2_add(dzh.y, s.ez),
-                          f2_add(vx.y, s.nvx), f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), ux1,
-                          uy1, uz1, m.y, eps2, js + 2, slot);
-      (void)dxl; (void)dyl; (void)dzl; (void)elx; (void)ely; (void)elz;
-      continue;
-    }
-    pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.x, s.ex), f2_add(dxl.x, elx)),
-                        f2_add(f2_add(dyh.x, s.ey), f2_add(dyl.x, ely)),
-                        f2_add(f2_add(dzh.x, s.ez), f2_add(dzl.x, elz)), f2_add(vx.x, s.nvx),
-                        f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), ux0, uy0, uz0, m.x, eps2, js,
-                        slot);
-    pair_tail<Sh, MASK>(s, f2_add(f2_add(dxh.y, s.ex), f2_add(dxl.y, elx)),
-                        f2_add(f2_add(dyh.y, s.ey), f2_add(dyl.y, ely)),
-                        f2_add(f2_add(dzh.y, s.ez), f2_add(dzl.y, elz)), f2_add(vx.y, s.nvx),
-                        f2_add(vy.y, s.nvy), f2_add(vz.y, s.nvz), ux1, uy1, uz1, m.y, eps2,
-                        js + 2, slot);
   }
 }
 
@@ -361,7 +394,7 @@ __device__ __forceinline__ f2 lanes_sum2(f2& a, f2& b) {
 }
 
 template <class Sh>
-__device__ __forceinline__ void flush(Target& s, Totals<Sh::SMT, Sh::NT, Sh::TC>& T,
+__device__ __forceinline__ void flush(TargetOf<Sh>& s, Totals<Sh::SMT, Sh::NT, Sh::TC>& T,
                                       float* col) {
   if constexpr (!Sh::JERK) {  // acceleration (and potential) only
     if constexpr (Sh::SMT) {
@@ -453,15 +486,19 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
     const int32_t b = l - it * B;
     const int64_t sk0 = a.soff[k];
     const int64_t S_k = a.soff[k + 1] - sk0;
-    const int64_t L = chunk_len(S_k, B, JT);
-    const int64_t j0 = sk0 + b * L;
-    const int64_t j1 = sk0 + min(S_k, (int64_t)(b + 1) * L);
+    // the item's j-chunk: chunk b of B of the cluster's sources, or of this
+    // process's piece of them in a j-partition
+    int64_t pb = 0, pe = S_k;
+    if (a.parts > 1) src_piece(S_k, a.part, a.parts, &pb, &pe);
+    const int64_t L = chunk_len(pe - pb, B, JT);
+    const int64_t j0 = sk0 + pb + b * L;
+    const int64_t j1 = sk0 + pb + min(pe - pb, (int64_t)(b + 1) * L);
     const int64_t tk0 = a.toff[k];
     const int32_t a0 = a.act_off[k];
     const int32_t m_k = a.act_off[k + 1] - a0;
     const int64_t p0 = a.off[k], p1 = a.off[k + 1];
 
-    Target tg[IPT];
+    TargetOf<Sh> tg[IPT];
     Totals<Sh::SMT, NT, TC> tot[IPT];
     bool valid[IPT];
     // warp wp owns the 32 * IPT consecutive targets [wp * 32 * IPT, ...):
@@ -516,15 +553,19 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       tg[r].ax = tg[r].ay = tg[r].az = 0ull;
       tg[r].jx = tg[r].jy = tg[r].jz = 0ull;
       tg[r].pt = 0ull;
-      tg[r].nax = bcast(-ax); tg[r].nay = bcast(-ay); tg[r].naz = bcast(-az);
-      tg[r].sx = tg[r].sy = tg[r].sz = 0ull;
+      if constexpr (Sh::SNAP) {
+        tg[r].nax = bcast(-ax); tg[r].nay = bcast(-ay); tg[r].naz = bcast(-az);
+        tg[r].sx = tg[r].sy = tg[r].sz = 0ull;
+      } else {
+        (void)ax; (void)ay; (void)az;
+      }
       tot[r].zero(tot_sh + r * 2 * TC * NT + tid);
     }
 
     // pipeline stages of SJ slots (the chunk starts on a tile boundary)
-    const int64_t ntile = ceil_div64(j1 - j0, SJ);
+    const int64_t ntile = ceil_div64(j1 - j0, SJ);  // 0: an empty piece
     uint32_t n_near = 0;  // cells this warp took on the near path
-    if (tid == 0) {
+    if (tid == 0 && ntile > 0) {
       issue_tile(stage[0], rec[0], stage_acc[0], &bar[0], src, tiles, gacc, j0,
                  min((int64_t)SJ, j1 - j0), tk0 + (j0 - sk0) / JT);
       pending[0] = true;

@@ -253,7 +253,13 @@ __device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p, bool 
   for (int32_t k = threadIdx.x; k < K; k += blockDim.x) {
     const int64_t mk = d.act_off[k + 1] - d.act_off[k];
     nit += (unsigned long long)ceil_div64(mk, p.NI);
-    inter += (unsigned long long)mk * (unsigned long long)(d.off[k + 1] - d.off[k]);
+    int64_t nk = d.off[k + 1] - d.off[k];
+    if (p.parts > 1) {  // the real particles of the piece (pad slots at the end)
+      int64_t pb, pe;
+      src_piece(d.soff[k + 1] - d.soff[k], p.part, p.parts, &pb, &pe);
+      nk = min(pe, nk) - min(pb, nk);
+    }
+    inter += (unsigned long long)mk * (unsigned long long)nk;
   }
   auto add = [](unsigned long long x, unsigned long long y) { return x + y; };
   nit = block_reduce<unsigned long long>(nit, add, shu, 0ull);
@@ -302,10 +308,16 @@ __device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p, bool 
     int32_t items = 0, wide = 0;
     if (k < K) {
       const int64_t mk = d.act_off[k + 1] - d.act_off[k];
-      const int64_t Sk = d.soff[k + 1] - d.soff[k];
+      int64_t Sk = d.soff[k + 1] - d.soff[k];
+      if (p.parts > 1) {  // B splits this process's piece of the sources
+        int64_t pb, pe;
+        src_piece(Sk, p.part, p.parts, &pb, &pe);
+        Sk = pe - pb;
+      }
       int64_t B = min((int64_t)bg, ceil_div64(Sk, p.JT));
       if (B < 1) B = 1;
-      B = ceil_div64(Sk, chunk_len(Sk, B, p.JT));  // every chunk non-empty
+      // every chunk non-empty (an empty piece: one empty chunk, zero sums)
+      if (Sk > 0) B = ceil_div64(Sk, chunk_len(Sk, B, p.JT));
       d.bfac[k] = static_cast<int32_t>(B);
       items = static_cast<int32_t>(ceil_div64(mk, p.NI) * B);
       if (B > kReduceSerial)  // (i-tile, row segment) units of k_reduce

@@ -111,6 +111,9 @@ struct PlanArgs {
   int grid;             // persistent CTAs of the force kernel
   int forced_b;         // fixed i-split factor (0: chosen here)
   int64_t part_items;   // capacity of the partial-sum buffer in work items
+  // j-partition: the force runs over piece `part` of `parts` of each
+  // cluster's sources (parts <= 1: all of them); B splits the piece
+  int part, parts;
   int step_mode;        // block step: adopt t_min as t_cur, reset t_min
   int count;            // add the interactions (and the step) to the counters
 };

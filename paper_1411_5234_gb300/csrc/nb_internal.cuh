@@ -126,6 +126,9 @@ struct ForceArgs {
   const void* src_c;
   double* out_snap; int ss;
   int comps;                // partial-sum components per target: 7, or 10 with snap
+  // j-partition: the sum runs over piece `part` of `parts` of every
+  // cluster's sources (src_piece); parts <= 1: all sources
+  int32_t part, parts;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -298,6 +301,21 @@ __host__ __device__ __forceinline__ int64_t round_up64(int64_t a, int64_t b) { r
 // so that every one of the B chunks is non-empty.
 __host__ __device__ __forceinline__ int64_t chunk_len(int64_t S_k, int64_t B, int64_t JT) {
   return round_up64(ceil_div64(S_k, B), JT);
+}
+
+// Piece `part` of `parts` of a cluster's S_k source slots, [*b, *e) relative
+// to the cluster's first slot: contiguous pieces of ceil(S_k / parts) slots
+// rounded up to a whole tile of both force kernels, so that every piece
+// starts on a tile; the last pieces may be empty.  The pieces of a
+// j-partition of the force sum (one per process).
+constexpr int kSrcPieceAlign = kMixJT;
+static_assert(kMixJT % kF64JT == 0, "a piece starts on a tile of both force kernels");
+__host__ __device__ __forceinline__ void src_piece(int64_t S_k, int32_t part, int32_t parts,
+                                                   int64_t* b, int64_t* e) {
+  const int64_t per = round_up64(ceil_div64(S_k, parts), kSrcPieceAlign);
+  const int64_t lo = (int64_t)part * per;
+  *b = lo < S_k ? lo : S_k;
+  *e = lo + per < S_k ? lo + per : S_k;
 }
 
 // ------------------------------------------------------- launch wrappers

@@ -28,8 +28,10 @@ FUNCTIONS = [
     "nb_profile_enable", "nb_profile_read", "nb_force_noalloc", "nb_tile_stats",
     "nb_energies", "nb_autotune", "nb_step_leapfrog", "nb_check_wait_timeout",
     "nb_noalloc_status", "nb_measure_rate", "nb_force_snap", "nb_correct_snap",
-    "nb_get_derivs", "nb_set_derivs",
+    "nb_get_derivs", "nb_set_derivs", "nb_source_piece", "nb_source_order", "nb_force_range",
+    "nb_block_force", "nb_block_correct", "nb_resort_sources",
 ]
+PIECE_ALIGN = 128     # NB_PIECE_ALIGN: slots per tile of a source piece
 
 
 class NbConfig(ctypes.Structure):
@@ -90,6 +92,12 @@ def _load() -> ctypes.CDLL:
         "nb_correct_snap": (ctypes.c_int, [P, i64, P, i64, P, P, P]),
         "nb_get_derivs": (ctypes.c_int, [P, P, P]),
         "nb_set_derivs": (ctypes.c_int, [P, P, P]),
+        "nb_source_piece": (ctypes.c_int, [i64, i32, i32, P, P]),
+        "nb_source_order": (ctypes.c_int, [P, P, P, P]),
+        "nb_force_range": (ctypes.c_int, [P, P, i64, i32, i32, P, P, P]),
+        "nb_block_force": (ctypes.c_int, [P, i32, i32, P, P, P, P]),
+        "nb_block_correct": (ctypes.c_int, [P]),
+        "nb_resort_sources": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -118,6 +126,15 @@ def default_config(**kw) -> NbConfig:
             raise AttributeError(f"nb_config has no field {k!r}")
         setattr(cfg, k, v)
     return cfg
+
+
+def source_piece(n_slots: int, part: int, n_parts: int) -> tuple[int, int]:
+    """Slot range [begin, end) of piece ``part`` of ``n_parts`` of a cluster
+    with ``n_slots`` source slots (nb_source_piece; host arithmetic)."""
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.nb_source_piece(int(n_slots), int(part), int(n_parts), ctypes.byref(b),
+                               ctypes.byref(e)), "nb_source_piece")
+    return b.value, e.value
 
 
 def workspace_size(n_total: int, n_clusters: int, cfg: NbConfig) -> int:
@@ -228,6 +245,62 @@ class Sim:
                "nb_force")
         self._order_outputs(acc, jerk, pot)
         return acc, jerk, pot
+
+    def force_range(self, active: torch.Tensor, part: int, n_parts: int,
+                    want_pot: bool = True, want_jerk: bool = True):
+        """Forces on ``active`` from piece ``part`` of ``n_parts`` of every
+        cluster's sources (nb_force_range): one process's share of a
+        j-partition; the sum over the parts is ``force``'s result."""
+        if active.dtype != torch.int32 or not active.is_cuda or not active.is_contiguous():
+            raise ValueError("active must be a contiguous int32 CUDA tensor")
+        m = active.numel()
+        acc = torch.empty((m, 3), dtype=torch.float64, device="cuda")
+        jerk = torch.empty((m, 3), dtype=torch.float64, device="cuda") if want_jerk else None
+        pot = torch.empty(m, dtype=torch.float64, device="cuda") if want_pot else None
+        self._order_inputs(active, acc, jerk, pot)
+        _check(lib.nb_force_range(self._ctx, _dptr(active), m, int(part), int(n_parts),
+                                  _dptr(acc), _dptr(jerk), _dptr(pot)), "nb_force_range")
+        self._order_outputs(acc, jerk, pot)
+        return acc, jerk, pot
+
+    def source_order(self):
+        """(particle of each source slot, -1 for padding; each cluster's
+        first slot), both host arrays (nb_source_order)."""
+        n = ctypes.c_int64()
+        _check(lib.nb_source_order(self._ctx, ctypes.byref(n), None, None), "nb_source_order")
+        perm = np.empty(n.value, dtype=np.int32)
+        soff = np.empty(self.n_clusters + 1, dtype=np.int64)
+        _check(lib.nb_source_order(self._ctx, ctypes.byref(n), _hptr(perm), _hptr(soff)),
+               "nb_source_order")
+        return perm, soff
+
+    def _rows(self, addr: int, m: int) -> torch.Tensor:
+        # (m, 4) float64 view of workspace rows at device address addr
+        off = addr - self.workspace.data_ptr()
+        if off < 0 or off % 8 or off + 32 * m > self.ws_bytes:
+            raise RuntimeError("step rows outside the workspace")
+        return self.workspace[off:off + 32 * m].view(torch.float64).view(m, 4)
+
+    def block_force(self, part: int = 0, n_parts: int = 1):
+        """First half of a block step (nb_block_force): returns the active
+        count m and the step's force rows -- [acc, jerk] or, in the 6th-order
+        scheme, [acc, jerk, snap] -- as (m, 4) float64 views of the
+        workspace (column 3 unused), to be summed over the processes of a
+        j-partition in place before ``block_correct``."""
+        m = ctypes.c_int64()
+        ptr = [ctypes.c_void_p() for _ in range(3)]
+        _check(lib.nb_block_force(self._ctx, int(part), int(n_parts), ctypes.byref(m),
+                                  *(ctypes.byref(p) for p in ptr)), "nb_block_force")
+        rows = [self._rows(p.value, m.value) for p in ptr if p.value]
+        return m.value, rows
+
+    def block_correct(self):
+        """Second half of a block step (nb_block_correct)."""
+        _check(lib.nb_block_correct(self._ctx), "nb_block_correct")
+
+    def resort_sources(self):
+        """Re-sort the source slots by the current positions (nb_resort_sources)."""
+        _check(lib.nb_resort_sources(self._ctx), "nb_resort_sources")
 
     def force_snap(self, active: torch.Tensor, want_pot: bool = True):
         """Acceleration, jerk, snap (and potential) of ``active`` from the last
