@@ -157,9 +157,13 @@ def workload_batch(args):
     # 1) the production run: graphs of 16 block steps
     sim = nbody.Sim(cl.pos, cl.vel, cl.mass, offsets=cl.offsets, eps=1e-4,
                     precision=nbody.NB_MIXED, level_min=3, graph_steps=16, **kw)
+    import tempfile
+    cache = os.path.join(tempfile.mkdtemp(prefix="nbody_tune_"), "tune.txt")
     if args.variant is None and not args.no_tune:
-        kw = {"variant": sim.autotune()[0]}
-        out["autotuned_variant"] = kw["variant"]
+        # the table per ceil(log2 m), cached for the second run below
+        out["autotuned_variant"] = sim.autotune(cache)[0]
+        v, b = sim.tune_table()
+        out["tune_table"] = {f"2^{k}": [int(v[k]), int(b[k])] for k in range(6, 16)}
     e0 = np.add(*sim.energies())
     secs, steps, _ = integrate(sim, t_end)
     st = sim.stats()
@@ -173,6 +177,8 @@ def workload_batch(args):
     # 2) the same run with force-kernel events (direct launches): its share
     sim = nbody.Sim(cl.pos, cl.vel, cl.mass, offsets=cl.offsets, eps=1e-4,
                     precision=nbody.NB_MIXED, level_min=3, graph_steps=0, **kw)
+    if args.variant is None and not args.no_tune:
+        sim.autotune(cache)   # the same table, from the cache
     sim.profile(True)
     secs2, _, _ = integrate(sim, t_end)
     fms, nlaunch = sim.profile_read()
@@ -640,9 +646,18 @@ def main():
                     level_min=L, level_max=L, graph_steps=0, **kw)
     stream = sim.stream
     tune = None
+    import tempfile
+    cache = os.path.join(tempfile.mkdtemp(prefix="nbody_tune_"), "tune.txt")
     if not args.no_tune and args.variant is None:
-        variant, tms = sim.autotune()
-        tune = {"chosen_variant": variant, "ms_per_variant_at_fraction_1_1/16_1/256": tms}
+        variant, tms = sim.autotune(cache)
+        tv, tb = sim.tune_table()
+        tune = {"table_ceil_log2_m": {f"2^{k}": [int(tv[k]), int(tb[k])]
+                                      for k in range(6, 21) if (1 << k) <= 2 * n},
+                "step_bucket": [int(tv[(n - 1).bit_length()]), int(tb[(n - 1).bit_length()])],
+                "ms_per_variant_at_m_every_4^k_th_slot": tms,
+                "cache": "written to a temporary file; the sweep below loads it"}
+    else:
+        cache = None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     sim.profile(True)
 
@@ -749,7 +764,7 @@ def main():
 
     # ---- nb_force sweep over the active fraction, mixed and FP64 ----
     if not args.no_sweep and rank == 0:
-        line["sweep"] = sweep(nbody, inputs, torch, cl)
+        line["sweep"] = sweep(nbody, inputs, torch, cl, cache)
     if not args.no_cpu and rank == 0 and world == 1:
         line["cpu_baseline"] = oracle_sample(cl, args.cpu_seconds)
     if rank == 0:
@@ -760,16 +775,20 @@ def main():
     return 0
 
 
-def sweep(nbody, inputs, torch, cl):
+def sweep(nbody, inputs, torch, cl, cache=None):
     n = cl.n
     out = {"unit": UNIT, "timing": "force kernel via CUDA events (nb_profile), best of 3",
            "mixed": [], "fp64": []}
     sims = {}
     for name, prec in (("mixed", nbody.NB_MIXED), ("fp64", nbody.NB_FP64)):
         s = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=prec, graph_steps=0)
+        if name == "mixed" and cache is not None:
+            s.autotune(cache)          # the headline's table, from its cache file
+            out["mixed_table"] = "autotune table per ceil(log2 m) (shape, B) in each entry"
         s.predict(0)
         s.profile(True)
         sims[name] = s
+    tv, tb = sims["mixed"].tune_table()
     for name, kmin, kmax in (("mixed", 10, 0), ("fp64", 10, 6)):
         s = sims[name]
         for k in range(kmin, kmax - 1, -1):
@@ -791,6 +810,8 @@ def sweep(nbody, inputs, torch, cl):
             if name == "mixed":
                 entry["frac_fp32_peak"] = (FLOPS_PER_INTERACTION * rate
                                            / fp32_peak_flops())
+                b = (m - 1).bit_length()
+                entry["shape_B"] = [int(tv[b]), int(tb[b])]
             out[name].append(entry)
     # acceleration only (nb_force with jerk == NULL), 20 flops per interaction
     out["mixed_acc_only"] = []

@@ -351,18 +351,41 @@ int nb_profile_read(nb_ctx *ctx, double *force_ms, int64_t *launches);
  * Synchronises. */
 int nb_tile_stats(nb_ctx *ctx, int64_t *warp_tiles, int64_t *near_warp_tiles);
 
-/* Autotuner: time every compiled shape of the mixed force kernel (see
- * nb_config.variant) on this context's own sources, for targets taken every
- * 1st, 16th and 256th source slot (the active fractions a block step sees),
- * and keep the shape with the least total time for the context's later
- * nb_force and nb_step_block calls.  variant_out (host, may be NULL) gets
- * the choice; ms_out (host, NB_TUNE_POINTS x variants doubles, may be NULL)
- * gets the timings [variant][fraction].  Uses the workspace's active-list
- * buffers (call it between steps); FP64 contexts return their shape.
- * Synchronises. */
-#define NB_TUNE_POINTS 3
-#define NB_MIXED_VARIANTS 6
-int nb_autotune(nb_ctx *ctx, int32_t *variant_out, double *ms_out);
+/* Autotuner: the shape of the mixed force kernel (nb_config.variant) and the
+ * i-split factor B (Sec. 2 item 3: the best Bfactor depends on the number of
+ * active particles and has to be chosen step by step), per ceil(log2 m) of
+ * the active count m -- a table of NB_TUNE_BUCKETS (variant, B) entries, B 0
+ * for the plan's own choice.  Measured on this context's own sources at
+ * m = every 4^k-th source slot (k = 0 .. NB_TUNE_POINTS-1, while m >= 64):
+ * every shape with the plan's B, then the fastest shape with B = 1, 2, 4, ...
+ * (the smallest B within 0.3 % of the fastest time is kept: fewer partial
+ * sums to write and reduce for the same speed).
+ * Buckets between two measured points take the nearer point's shape, and its
+ * B scaled by the ratio of the active counts (the same fill of the grid).
+ * nb_force then takes the entry of its m, and the plan of every block step
+ * the entry of the step's active count (on the device: a block step launches
+ * every shape the table holds, and each one exits at once unless the plan
+ * chose it).  cache_path (may be NULL): a text file of tables, one line per
+ * problem class (GPU name, SM count, precision, Hermite order, ceil(log2 N),
+ * cluster count); a table found there is applied without measuring, and a
+ * measured one is appended.  variant_out (host, may be NULL): the shape of
+ * the largest bucket (also the context's nb_config.variant from now on);
+ * ms_out (host, may be NULL): NB_TUNE_POINTS x NB_MIXED_VARIANTS doubles,
+ * the time of each shape at each point with the plan's B (0: not measured).
+ * Uses the workspace's active-list buffers (call it between steps).  Mixed
+ * precision only (other precisions have one shape and return it).
+ * Synchronises; NB_EINVAL when a measured table cannot be appended to
+ * cache_path (the table is applied all the same). */
+#define NB_TUNE_POINTS 8
+#define NB_TUNE_BUCKETS 32
+#define NB_MIXED_VARIANTS 8
+int nb_autotune(nb_ctx *ctx, const char *cache_path, int32_t *variant_out, double *ms_out);
+
+/* The context's autotune table (host arrays of NB_TUNE_BUCKETS entries,
+ * either may be NULL): the shape and B (0: the plan's choice) used for
+ * active counts m with ceil(log2 m) = bucket.  Before nb_autotune every
+ * entry is (nb_config.variant, nb_config.bfactor). */
+int nb_tune_table(nb_ctx *ctx, int32_t *variant_by_bucket, int32_t *bfactor_by_bucket);
 
 /* Arithmetic-rate probe for the roofline of the force kernels (the paper has
  * no counterpart): runs independent FMA chains in 4 CTAs of 256 threads per

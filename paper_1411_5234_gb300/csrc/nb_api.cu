@@ -5,9 +5,11 @@
 // allocated here; the caller's workspace is carved into the arrays below.
 #include <climits>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -36,7 +38,7 @@ struct Layout {
   size_t snap, crackle, snap_new, src_acc_mix, src64_acc;  // 6th order only (else empty)
   size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
       src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, wt_off, wide_cnt, bfac, esum,
-      status, counters, t_end, work, tiles, toff, sperm, sinv, mark, rows, total;
+      status, counters, t_end, work, tune, sel, tiles, toff, sperm, sinv, mark, rows, total;
   int64_t S, part_items, n_tiles;
 };
 
@@ -85,6 +87,8 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles, int order) 
   L.counters = take(c, 8 * 4);
   L.t_end = take(c, 8);
   L.work = take(c, 4);
+  L.tune = take(c, 8 * (size_t)kTuneBuckets);
+  L.sel = take(c, 8);
   L.tiles = take(c, 16 * kTileRecF4 * (size_t)n_tiles);
   L.toff = take(c, 4 * ((size_t)K + 1));
   L.sperm = take(c, 4 * (size_t)S);
@@ -206,6 +210,11 @@ struct nb_ctx {
   Layout L{};
   cudaStream_t st = nullptr;
   int grid_mix = 0, grid_f64 = 0, grid_acc = 0, grid_snap = 0, sms = 0;
+  int grid_v[kMixVariants] = {};  // persistent CTAs of each mixed shape
+  // autotune table, host copy: (variant, B) per ceil(log2 m); `tabled` once
+  // nb_autotune filled it (nb_force and block steps then follow it)
+  std::vector<int32_t> tune_host;
+  bool tabled = false;
   std::vector<int64_t> off_host;
   std::vector<double> mass_host;
   std::vector<int32_t> sperm_host;  // source slot order (for the autotuner's target lists)
@@ -281,6 +290,8 @@ ForceArgs force_args(nb_ctx* c, const int32_t* active, const int32_t* rows, doub
   a.out_snap = nullptr;
   a.ss = 0;
   a.comps = kPartialComps;
+  a.sel = nullptr;
+  a.my_variant = c->cfg.variant;
   a.part = c->part;
   a.parts = c->parts;
   return a;
@@ -300,15 +311,42 @@ struct PieceScope {
   }
 };
 
+// The autotune table's bucket of an active count: ceil(log2 m).
+int tune_bucket(int64_t m) {
+  int b = 0;
+  while (b < kTuneBuckets - 1 && ((int64_t)1 << b) < m) ++b;
+  return b;
+}
+
+// Whether a force evaluation of this context takes its mixed shape from the
+// autotune table (the plain mixed path with jerk, once nb_autotune ran).
+bool uses_table(const nb_ctx* c, bool f64, bool acc_only, bool snap) {
+  return c->tabled && !f64 && !acc_only && !snap && sep_mode(c) == 0;
+}
+
+// variant, forced_b: the mixed shape and i-split to plan for (-1: the
+// context's); device_select: the plan takes both from the table instead.
 PlanArgs plan_args(nb_ctx* c, bool f64, int step_mode, int count, bool acc_only = false,
-                   bool snap = false) {
+                   bool snap = false, int variant = -1, int forced_b = -1,
+                   bool device_select = false) {
+  if (variant < 0) variant = c->cfg.variant;
+  if (forced_b < 0) forced_b = c->cfg.bfactor;
   PlanArgs p{};
   p.NI = f64 ? kF64NI
              : snap ? force_mixed_snap_ni()
-                    : acc_only ? force_mixed_acc_ni() : force_mixed_ni(c->cfg.variant);
+                    : acc_only ? force_mixed_acc_ni() : force_mixed_ni(variant);
   p.JT = f64 ? kF64JT : kMixJT;
-  p.grid = f64 ? c->grid_f64 : snap ? c->grid_snap : acc_only ? c->grid_acc : c->grid_mix;
-  p.forced_b = c->cfg.bfactor;
+  p.grid = f64        ? c->grid_f64
+           : snap     ? c->grid_snap
+           : acc_only ? c->grid_acc
+           : sep_mode(c) ? c->grid_mix
+                         : c->grid_v[variant];
+  p.forced_b = forced_b;
+  p.use_table = device_select ? 1 : 0;
+  for (int v = 0; v < kMixVariants; ++v) {
+    p.ni_v[v] = force_mixed_ni(v);
+    p.grid_v[v] = c->grid_v[v];
+  }
   p.part_items = c->L.part_items;
   p.step_mode = step_mode;
   p.count = count;
@@ -361,20 +399,33 @@ cudaError_t prof_events(nb_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
 }
 
 // plan + force + partial reduce on the active list already described by
-// act_off (and `active`, or the identity when null).
+// act_off (and `active`, or the identity when null).  m_host: the active
+// count when the host knows it (nb_force: the table entry is applied here);
+// -1 for a block step, whose plan (`planned`) picks the entry on the device.
 cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows, double* acc,
                           int sa, double* jerk, int sj, double* pot, int sp, bool f64,
                           int step_mode, int count, bool pot_only, int64_t m_bound,
-                          bool planned = false) {
+                          bool planned = false, int64_t m_host = -1) {
   cudaError_t e = cudaSuccess;
   // no jerk wanted (and not the FP64 energy pass): the mixed path runs the
   // acceleration-only kernel
   const bool acc_only = !f64 && jerk == nullptr;
+  const bool tabled = uses_table(c, f64, acc_only, false);
+  int variant = c->cfg.variant, forced_b = c->cfg.bfactor;
+  if (tabled && m_host >= 0) {
+    const int b = tune_bucket(m_host);
+    variant = c->tune_host[2 * b];
+    if (forced_b == 0) forced_b = c->tune_host[2 * b + 1];
+  }
+  const bool device_select = tabled && m_host < 0;
   if (!planned) {
-    e = launch_plan(c->d, plan_args(c, f64, step_mode, count, acc_only), c->st);
+    e = launch_plan(c->d, plan_args(c, f64, step_mode, count, acc_only, false, variant, forced_b,
+                                    device_select),
+                    c->st);
     if (e != cudaSuccess) return e;
   }
   ForceArgs fa = force_args(c, active, rows, acc, sa, jerk, sj, pot, sp, f64);
+  fa.my_variant = variant;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (c->prof) {
     e = prof_events(c, &ev);
@@ -388,15 +439,28 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
     e = launch_force_mixed_acc(fa, c->grid_acc, pot != nullptr, c->st);
   else if (sep_mode(c))
     e = launch_force_mixed_sep(fa, c->grid_mix, pot != nullptr, sep_mode(c), c->st);
-  else
-    e = launch_force_mixed(fa, c->grid_mix, pot != nullptr, c->cfg.variant, c->st);
+  else if (device_select) {
+    // every distinct shape of the table; each exits at once unless the plan
+    // chose it for this step's active count
+    fa.sel = c->d.sel;
+    bool launched[kMixVariants] = {};
+    for (int b = 0; b < kTuneBuckets && e == cudaSuccess; ++b) {
+      const int v = c->tune_host[2 * b];
+      if (launched[v]) continue;
+      launched[v] = true;
+      fa.my_variant = v;
+      e = launch_force_mixed(fa, c->grid_v[v], pot != nullptr, v, c->st);
+    }
+  } else {
+    e = launch_force_mixed(fa, c->grid_v[variant], pot != nullptr, variant, c->st);
+  }
   if (e != cudaSuccess) return e;
   if (c->prof) {
     e = cudaEventRecord(ev.second, c->st);
     if (e != cudaSuccess) return e;
     c->ev_pending.push_back(ev);
   }
-  const int ni = f64 ? kF64NI : acc_only ? force_mixed_acc_ni() : force_mixed_ni(c->cfg.variant);
+  const int ni = f64 ? kF64NI : acc_only ? force_mixed_acc_ni() : force_mixed_ni(variant);
   return launch_reduce(fa, ni, !pot_only, m_bound, c->sms, c->st);
 }
 
@@ -451,7 +515,8 @@ cudaError_t enqueue_block_force(nb_ctx* c) {
   e = launch_predict(c->d, c->d.t_min, 0, T, !f64, f64, true, c->st);
   if (e != cudaSuccess) return e;
   const bool o6 = c->cfg.order == 6;
-  e = launch_scan_plan_scatter(c->d, plan_args(c, f64, 1, 1, false, o6), T, c->st);
+  e = launch_scan_plan_scatter(
+      c->d, plan_args(c, f64, 1, 1, false, o6, -1, -1, uses_table(c, f64, false, o6)), T, c->st);
   if (e != cudaSuccess) return e;
   double* an = reinterpret_cast<double*>(c->d.acc_new);
   double* jn = reinterpret_cast<double*>(c->d.jerk_new);
@@ -510,6 +575,87 @@ bool finite_all(const double* x, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
     if (!std::isfinite(x[i])) return false;
   return true;
+}
+
+
+// ---- autotune table: cache key, cache file, application
+
+// The problem class a table belongs to: the GPU (name, SMs), the precision
+// and Hermite order, ceil(log2 N) and the number of clusters.
+std::string tune_key(const nb_ctx* c) {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  std::string name = "unknown";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+    name = prop.name;
+  for (char& ch : name)
+    if (ch == ' ' || ch == '=' || ch == ';') ch = '_';
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "nbody-tune-1 gpu=%s sms=%d prec=%d order=%d logN=%d K=%d",
+                name.c_str(), c->sms, c->cfg.precision, c->cfg.order, tune_bucket(c->d.N),
+                c->d.K);
+  return buf;
+}
+
+// The last line of `path` with this key: "<key> table=v,b;v,b;..." with
+// kTuneBuckets valid entries.
+bool tune_load(const char* path, const std::string& key, std::vector<int32_t>& tab) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  bool found = false;
+  std::vector<char> line(1 << 16);
+  while (std::fgets(line.data(), static_cast<int>(line.size()), f)) {
+    std::string s(line.data());
+    while (!s.empty() && (s.back() == '\n' || s.back() == '\r')) s.pop_back();
+    const size_t pos = s.find(" table=");
+    if (pos == std::string::npos || s.compare(0, pos, key) != 0 || pos != key.size()) continue;
+    std::vector<int32_t> t;
+    const char* p = s.c_str() + pos + 7;
+    bool ok = true;
+    for (int b = 0; b < kTuneBuckets && ok; ++b) {
+      int v = -1, bf = -1, n = 0;
+      ok = std::sscanf(p, "%d,%d%n", &v, &bf, &n) == 2 && v >= 0 && v < kMixVariants &&
+           bf >= 0 && bf <= (1 << 20);
+      if (!ok) break;
+      t.push_back(v);
+      t.push_back(bf);
+      p += n;
+      if (b + 1 < kTuneBuckets) ok = *p++ == ';';
+    }
+    if (ok) {
+      tab = t;
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+bool tune_save(const char* path, const std::string& key, const std::vector<int32_t>& tab) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) return false;
+  std::fprintf(f, "%s table=", key.c_str());
+  for (int b = 0; b < kTuneBuckets; ++b)
+    std::fprintf(f, "%d,%d%s", tab[2 * b], tab[2 * b + 1], b + 1 < kTuneBuckets ? ";" : "\n");
+  return std::fclose(f) == 0;
+}
+
+// Make c->tune_host the context's table: on the device for the block steps'
+// plan, the shape of the largest bucket as the context's own, and graphs
+// captured with the old shapes dropped.
+cudaError_t tune_apply(nb_ctx* c) {
+  cudaError_t e = cudaMemcpyAsync(c->d.tune, c->tune_host.data(), 8 * (size_t)kTuneBuckets,
+                                  cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(c->st);  // the host copy may change after this
+  if (e != cudaSuccess) return e;
+  c->tabled = true;
+  c->cfg.variant = c->tune_host[2 * tune_bucket(c->d.N)];
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -610,6 +756,8 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   d.counters = reinterpret_cast<unsigned long long*>(w + c->L.counters);
   d.t_end = reinterpret_cast<int64_t*>(w + c->L.t_end);
   d.work_ctr = reinterpret_cast<int32_t*>(w + c->L.work);
+  d.tune = reinterpret_cast<int32_t*>(w + c->L.tune);
+  d.sel = reinterpret_cast<int32_t*>(w + c->L.sel);
   d.order = cfg->order;
   if (cfg->order == 6) {
     d.snap = reinterpret_cast<dbl4*>(w + c->L.snap);
@@ -634,6 +782,12 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   }
   c->grid_mix = sep_mode(c) ? sms * force_mixed_sep_ctas_per_sm(sep_mode(c))
                             : sms * force_mixed_ctas_per_sm(c->cfg.variant);
+  for (int v = 0; v < kMixVariants; ++v) c->grid_v[v] = sms * force_mixed_ctas_per_sm(v);
+  c->tune_host.assign(2 * kTuneBuckets, 0);
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    c->tune_host[2 * b] = c->cfg.variant;
+    c->tune_host[2 * b + 1] = c->cfg.bfactor;
+  }
   c->grid_f64 = sms * force_fp64_ctas_per_sm();
   c->grid_acc = sms * force_mixed_acc_ctas_per_sm();
   c->grid_snap = sms * force_mixed_snap_ctas_per_sm();
@@ -683,6 +837,8 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
         cudaMemsetAsync(d.status, 0, 4, st) || cudaMemsetAsync(d.counters, 0, 32, st) ||
         cudaMemsetAsync(d.wide_cnt, 0, 4 * (size_t)wide_counter_entries(c->L.part_items), st) ||
         cudaMemsetAsync(d.mark, 0xff, 4 * N, st) ||
+        cudaMemcpyAsync(d.tune, c->tune_host.data(), 8 * (size_t)kTuneBuckets,
+                        cudaMemcpyHostToDevice, st) ||
         (cfg->order == 6 && (cudaMemsetAsync(d.snap, 0, 32 * N, st) ||
                              cudaMemsetAsync(d.crackle, 0, 32 * N, st)))) {
       rc = NB_ECUDA;
@@ -755,7 +911,8 @@ int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, doubl
   const bool f64 = !is_mixed(c);
   // targets in source-slot order (spatially coherent warps), rows mapped back
   NB_TRY(launch_list_to_slots(c->d, active_idx, m, c->st));
-  NB_TRY(enqueue_force(c, c->d.active, c->d.rows, acc, 3, jerk, 3, pot, 1, f64, 0, 1, false, m));
+  NB_TRY(enqueue_force(c, c->d.active, c->d.rows, acc, 3, jerk, 3, pot, 1, f64, 0, 1, false, m,
+                       false, m));
   return NB_OK;
 }
 
@@ -1183,93 +1340,158 @@ int nb_tile_stats(nb_ctx* c, int64_t* warp_tiles, int64_t* near_warp_tiles) {
   return NB_OK;
 }
 
-int nb_autotune(nb_ctx* c, int32_t* variant_out, double* ms_out) {
+int nb_autotune(nb_ctx* c, const char* cache_path, int32_t* variant_out, double* ms_out) {
   NvtxRange nvtx_range("nb_autotune");
   if (!c) return NB_EINVAL;
+  if (c->block_open) return NB_ESTATE;
+  if (ms_out)
+    for (int q = 0; q < NB_TUNE_POINTS * kMixVariants; ++q) ms_out[q] = 0.0;
   if (c->cfg.precision != NB_MIXED) {  // FP64, DS, FP32: one shape each, nothing to choose
     if (variant_out) *variant_out = c->cfg.variant;
     return NB_OK;
   }
+  const std::string key = tune_key(c);
+  std::vector<int32_t> tab;
+  if (cache_path && tune_load(cache_path, key, tab)) {
+    c->tune_host = tab;
+    NB_TRY(tune_apply(c));
+    if (variant_out) *variant_out = c->cfg.variant;
+    return sync_status(c);
+  }
   Dev& d = c->d;
-  const int nv = force_mixed_variants();
-  const int fracs[3] = {1, 16, 256};
-  std::vector<double> ms(static_cast<size_t>(nv) * 3, 0.0);
+  const int saved_b = c->cfg.bfactor;
+  c->tabled = false;  // every timed launch below runs the shape and B it is given
   cudaEvent_t e0, e1;
   NB_TRY(cudaEventCreate(&e0));
   NB_TRY(cudaEventCreate(&e1));
-  const int saved = c->cfg.variant;
-  int rc = NB_OK;
   double* an = reinterpret_cast<double*>(d.acc_new);
   double* jn = reinterpret_cast<double*>(d.jerk_new);
-  for (int fi = 0; fi < 3 && rc == NB_OK; ++fi) {
-    // every fracs[fi]-th source slot of each cluster, in slot order
+  std::vector<int64_t> soff(d.K + 1, 0);
+  for (int32_t k = 0; k < d.K; ++k)
+    soff[k + 1] = soff[k] + round_up64(c->off_host[k + 1] - c->off_host[k], 4);
+  int rc = NB_OK;
+  // one launch of shape v with split B on the current list: its time (ms);
+  // launches under 5 ms are repeated and the best of five is kept
+  auto time_one = [&](int v, int B, double* out) -> bool {
+    c->cfg.variant = v;
+    c->cfg.bfactor = B;
+    double best = 1e30;
+    for (int r = 0; r < 5; ++r) {
+      if (cudaEventRecord(e0, c->st) ||
+          enqueue_force(c, d.active, nullptr, an, 4, jn, 4, nullptr, 0, false, 0, 0, false,
+                        d.N) ||
+          cudaEventRecord(e1, c->st) || cudaEventSynchronize(e1))
+        return false;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      best = std::min(best, (double)t);
+      if (best >= 5.0) break;
+    }
+    *out = best;
+    return true;
+  };
+  struct Point { int64_t m; int v, B; };
+  std::vector<Point> pts;
+  for (int k = 0; k < NB_TUNE_POINTS && rc == NB_OK; ++k) {
+    // every 4^k-th source slot of each cluster, in slot order
+    const int64_t stride = (int64_t)1 << (2 * k);
     std::vector<int32_t> list;
     std::vector<int32_t> aoff(d.K + 1, 0);
-    std::vector<int64_t> soff(d.K + 1, 0);
-    for (int32_t k = 0; k < d.K; ++k)
-      soff[k + 1] = soff[k] + round_up64(c->off_host[k + 1] - c->off_host[k], 4);
-    for (int32_t k = 0; k < d.K; ++k) {
-      aoff[k] = static_cast<int32_t>(list.size());
-      for (int64_t sl = soff[k]; sl < soff[k + 1]; sl += fracs[fi])
+    int64_t nit_max = 0;
+    for (int32_t q = 0; q < d.K; ++q) {
+      aoff[q] = static_cast<int32_t>(list.size());
+      for (int64_t sl = soff[q]; sl < soff[q + 1]; sl += stride)
         if (c->sperm_host[sl] >= 0) list.push_back(c->sperm_host[sl]);
     }
     aoff[d.K] = static_cast<int32_t>(list.size());
-    if (list.empty()) continue;
+    const int64_t m = static_cast<int64_t>(list.size());
+    if (m == 0 || (k > 0 && m < 64)) break;
     if (cudaMemcpyAsync(d.active, list.data(), 4 * list.size(), cudaMemcpyHostToDevice, c->st) ||
         cudaMemcpyAsync(d.act_off, aoff.data(), 4 * aoff.size(), cudaMemcpyHostToDevice, c->st) ||
         cudaStreamSynchronize(c->st)) {
       rc = NB_ECUDA;
       break;
     }
-    for (int v = 0; v < nv && rc == NB_OK; ++v) {
-      c->cfg.variant = v;
-      int dev = 0, sms = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      c->grid_mix = sms * force_mixed_ctas_per_sm(v);
-      float best = 1e30f;
-      for (int r = 0; r < 3; ++r) {  // one warm-up, best of two
-        if (cudaEventRecord(e0, c->st) ||
-            enqueue_force(c, d.active, nullptr, an, 4, jn, 4, nullptr, 0, false, 0, 0, false,
-                          d.N) ||
-            cudaEventRecord(e1, c->st) || cudaEventSynchronize(e1)) {
-          rc = NB_ECUDA;
-          break;
-        }
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (r > 0 && t < best) best = t;
-      }
-      ms[static_cast<size_t>(v) * 3 + fi] = best;
+    double warm = 0.0;
+    if (!time_one(kMixDefaultVariant, 0, &warm)) { rc = NB_ECUDA; break; }
+    // every shape with the plan's B
+    int vbest = 0;
+    double tbest = 1e30;
+    for (int v = 0; v < kMixVariants; ++v) {
+      double t = 0.0;
+      if (!time_one(v, 0, &t)) { rc = NB_ECUDA; break; }
+      if (ms_out) ms_out[k * kMixVariants + v] = t;
+      if (t < tbest) { tbest = t; vbest = v; }
     }
+    if (rc != NB_OK) break;
+    const double ms_best_plan = tbest;
+    // the fastest shape with B = 1, 2, 4, ... up to the partial-sum buffer's
+    // capacity (the plan's own cap) and the clusters' tile counts
+    const int ni = force_mixed_ni(vbest);
+    for (int32_t q = 0; q < d.K; ++q) nit_max += ceil_div64(aoff[q + 1] - aoff[q], ni);
+    const int64_t bcap = std::min<int64_t>(
+        {c->L.part_items / std::max<int64_t>(nit_max, 1), ceil_div64(d.N, kMixJT), 4096});
+    // the smallest B within 0.3 % of the fastest (timing noise): fewer
+    // partial sums written and reduced for the same speed; the plan's own
+    // choice (B = 0) last
+    std::vector<std::pair<int, double>> cand;
+    for (int64_t B = 1; B <= bcap && rc == NB_OK; B *= 2) {
+      double t = 0.0;
+      if (!time_one(vbest, static_cast<int>(B), &t)) { rc = NB_ECUDA; break; }
+      cand.push_back({static_cast<int>(B), t});
+      tbest = std::min(tbest, t);
+    }
+    if (rc != NB_OK) break;
+    cand.push_back({0, ms_best_plan});
+    int bbest = 0;
+    for (const auto& cb : cand)
+      if (cb.second <= tbest * 1.003) {
+        bbest = cb.first;
+        break;
+      }
+    pts.push_back({m, vbest, bbest});
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  int choice = saved;
-  if (rc == NB_OK) {
-    double best = 1e300;
-    for (int v = 0; v < nv; ++v) {
-      const double tot = ms[v * 3] + ms[v * 3 + 1] + ms[v * 3 + 2];
-      if (tot < best) {
-        best = tot;
-        choice = v;
-      }
+  c->cfg.bfactor = saved_b;
+  if (rc != NB_OK || pts.empty()) {
+    c->tabled = false;
+    c->cfg.variant = c->tune_host.empty() ? kMixDefaultVariant : c->tune_host[2 * tune_bucket(d.N)];
+    return rc != NB_OK ? rc : sync_status(c);
+  }
+  // every bucket from the measured point nearest in log2 m (ties: the larger
+  // m); B scaled by the ratio of the active counts, the same fill of the grid
+  tab.assign(2 * kTuneBuckets, 0);
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    size_t best = 0;
+    double dist = 1e30;
+    for (size_t q = 0; q < pts.size(); ++q) {
+      const double dq = std::fabs(std::log2((double)pts[q].m) - b);
+      if (dq < dist - 1e-9) { dist = dq; best = q; }
     }
+    const Point& p = pts[best];
+    int B = p.B;
+    if (B > 0) {
+      const double scaled = p.B * (double)p.m / std::ldexp(1.0, b);
+      B = static_cast<int>(std::min(4096.0, std::max(1.0, std::floor(scaled + 0.5))));
+    }
+    tab[2 * b] = p.v;
+    tab[2 * b + 1] = B;
   }
-  c->cfg.variant = choice;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  c->grid_mix = sms * force_mixed_ctas_per_sm(choice);
-  if (c->graph) {  // captured with the previous shape
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
-  if (variant_out) *variant_out = choice;
-  if (ms_out)
-    for (size_t q = 0; q < ms.size(); ++q) ms_out[q] = ms[q];
-  if (rc != NB_OK) return rc;
+  c->tune_host = tab;
+  NB_TRY(tune_apply(c));
+  if (variant_out) *variant_out = c->cfg.variant;
+  if (cache_path && !tune_save(cache_path, key, tab)) return NB_EINVAL;
   return sync_status(c);
+}
+
+int nb_tune_table(nb_ctx* c, int32_t* variant_by_bucket, int32_t* bfactor_by_bucket) {
+  if (!c) return NB_EINVAL;
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    if (variant_by_bucket) variant_by_bucket[b] = c->tune_host[2 * b];
+    if (bfactor_by_bucket) bfactor_by_bucket[b] = c->tune_host[2 * b + 1];
+  }
+  return NB_OK;
 }
 
 int nb_status(nb_ctx* c) {

@@ -12,6 +12,10 @@
 //   3:  32 x 4 (one warp per CTA, 8 CTAs per SM), one tile per stage
 //   4:  64 x 3, two tiles per stage (10 warps per SM)
 //   5: 128 x 2, totals in registers, source loop unrolled x2, two tiles per stage
+//   6:  64 x 2 (8 CTAs per SM), one tile per stage: 128 targets per work item
+//   7:  32 x 2 (16 CTAs per SM), one tile per stage: 64 targets per work item
+// (6 and 7 serve small active sets: fewer targets per item means more
+// i-tiles and fewer source chunks for the same grid)
 // and, for nb_force calls that want no jerk, one acceleration-only shape.
 #include "../../include/nbody_gb300.h"
 #include "nb_force_mixed.cuh"
@@ -24,6 +28,8 @@ template <bool POT> using S2 = mixk::MixShape<64, 4, POT, false, true, 1, 4, tru
 template <bool POT> using S3 = mixk::MixShape<32, 4, POT, false, true, 1, 8, true, mixk::kSepMixed, 4, 1>;
 template <bool POT> using S4 = mixk::MixShape<64, 3, POT, false, true, 1, 5, true, mixk::kSepMixed, 4, 2>;
 template <bool POT> using S5 = mixk::MixShape<128, 2, POT, false, false, 2, 2, true, mixk::kSepMixed, 4, 2>;
+template <bool POT> using S6 = mixk::MixShape<64, 2, POT, false, true, 1, 8, true, mixk::kSepMixed, 4, 1>;
+template <bool POT> using S7 = mixk::MixShape<32, 2, POT, false, true, 1, 16, true, mixk::kSepMixed, 4, 1>;
 // acceleration (and potential) only: 64 x 4 at 6 CTAs per SM was the fastest
 // of the 64x4 (5 or 6 CTAs/SM, unrolled or not), 128x2 and 256x1 shapes at
 // N = m = 2^20 (measured on GB300)
@@ -56,6 +62,9 @@ int occupancy_both() {
 }
 }  // namespace
 
+static_assert(kMixVariants == NB_MIXED_VARIANTS, "the shapes the ABI announces");
+static_assert(kTuneBuckets == NB_TUNE_BUCKETS, "the autotune table the ABI announces");
+
 int force_mixed_variants() { return NB_MIXED_VARIANTS; }
 
 int force_mixed_ni(int variant) {
@@ -65,6 +74,8 @@ int force_mixed_ni(int variant) {
     case 3: return S3<false>::NI;
     case 4: return S4<false>::NI;
     case 5: return S5<false>::NI;
+    case 6: return S6<false>::NI;
+    case 7: return S7<false>::NI;
     default: return S0<false>::NI;
   }
 }
@@ -77,6 +88,8 @@ cudaError_t launch_force_mixed(const ForceArgs& a, int grid, bool with_pot, int 
     case 3: return with_pot ? launch_shape<S3<true>>(a, grid, st) : launch_shape<S3<false>>(a, grid, st);
     case 4: return with_pot ? launch_shape<S4<true>>(a, grid, st) : launch_shape<S4<false>>(a, grid, st);
     case 5: return with_pot ? launch_shape<S5<true>>(a, grid, st) : launch_shape<S5<false>>(a, grid, st);
+    case 6: return with_pot ? launch_shape<S6<true>>(a, grid, st) : launch_shape<S6<false>>(a, grid, st);
+    case 7: return with_pot ? launch_shape<S7<true>>(a, grid, st) : launch_shape<S7<false>>(a, grid, st);
     default: return with_pot ? launch_shape<S0<true>>(a, grid, st) : launch_shape<S0<false>>(a, grid, st);
   }
 }
@@ -88,6 +101,8 @@ int force_mixed_ctas_per_sm(int variant) {
     case 3: return occupancy_both<S3>();
     case 4: return occupancy_both<S4>();
     case 5: return occupancy_both<S5>();
+    case 6: return occupancy_both<S6>();
+    case 7: return occupancy_both<S7>();
     default: return occupancy_both<S0>();
   }
 }

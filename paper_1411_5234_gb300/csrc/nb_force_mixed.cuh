@@ -448,6 +448,9 @@ template <class Sh>
 __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArgs a) {
   constexpr int NT = Sh::NT, IPT = Sh::IPT, NI = Sh::NI;
   constexpr int SJ = Sh::ST * JT;  // sources per pipeline stage
+  // a block step launches every shape of its autotune table; only the one
+  // the plan chose for this step's active count works
+  if (a.sel && a.sel[0] != a.my_variant) return;
   __shared__ __align__(128) float4 stage[2][Sh::ST * kTileF4];
   __shared__ __align__(16) float4 rec[2][Sh::ST * kTileRecF4];
   __shared__ __align__(8) uint64_t bar[2];

@@ -242,11 +242,31 @@ __global__ void __launch_bounds__(kMixJT) k_scatter_tiles(Dev d, int T) {
 // cluster's new block time t_min[k] becomes t_cur[k]; t_min itself is reset
 // here (reset_tmin) or, when the active list is still to be built from it,
 // by the step's corrector.
-__device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p, bool reset_tmin) {
+__device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p0, bool reset_tmin) {
   __shared__ unsigned long long shu[32];
   __shared__ int32_t shi[32];
   __shared__ int32_t bg_sh;
+  __shared__ int32_t var_sh;
   const int32_t K = d.K;
+  PlanArgs p = p0;
+  if (p0.use_table) {
+    // the shape and split of the autotune table for ceil(log2 m) of the
+    // step's active count (the list is complete: act_off is final here)
+    if (threadIdx.x == 0) {
+      const int32_t m = d.act_off[K] - d.act_off[0];
+      const int b = m <= 1 ? 0 : min(kTuneBuckets - 1, 32 - __clz(m - 1));
+      const int v = d.tune[2 * b];
+      var_sh = v;
+      bg_sh = d.tune[2 * b + 1];
+      d.sel[0] = v;
+      d.sel[1] = p0.ni_v[v];
+    }
+    __syncthreads();
+    p.NI = p0.ni_v[var_sh];
+    p.grid = p0.grid_v[var_sh];
+    p.forced_b = p0.forced_b > 0 ? p0.forced_b : bg_sh;  // a configured B wins
+    __syncthreads();  // bg_sh is rewritten below
+  }
   // the force kernel's dynamic item counter starts from zero every launch
   if (threadIdx.x == 0 && d.work_ctr) *d.work_ctr = 0;
   unsigned long long nit = 0, inter = 0;
@@ -405,6 +425,7 @@ __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
   extern __shared__ double red[];  // [component][row r][lane]
   __shared__ int last_sh;
   const int32_t K = a.K;
+  if (a.sel) NI = a.sel[1];  // the shape the plan chose (block steps with a table)
   // small splits: one lane per target
   const int32_t m = a.act_off[K];
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {

@@ -114,6 +114,12 @@ struct PlanArgs {
   // j-partition: the force runs over piece `part` of `parts` of each
   // cluster's sources (parts <= 1: all of them); B splits the piece
   int part, parts;
+  // autotune table (block steps of the mixed path; 0: not used): the plan
+  // takes (variant, B) from d.tune for ceil(log2 m) of the step's active
+  // count, the variant's NI and grid from these arrays, and records the
+  // choice in d.sel
+  int use_table;
+  int ni_v[kMixVariants], grid_v[kMixVariants];
   int step_mode;        // block step: adopt t_min as t_cur, reset t_min
   int count;            // add the interactions (and the step) to the counters
 };

@@ -39,6 +39,8 @@ constexpr int kMixJT = 128;          // sources per shared-memory tile (multiple
 constexpr int kMixJD = 64;           // sources per cell (one centre/radius record)
 constexpr int kMixCells = kMixJT / kMixJD;  // cells per tile
 constexpr int kMixDefaultVariant = 0;       // mixed kernel shape of nb_default_config
+constexpr int kMixVariants = 8;             // compiled mixed kernel shapes
+constexpr int kTuneBuckets = 32;            // autotune table: one entry per ceil(log2 m)
 constexpr int kTileRecF4 = 2 * kMixCells;   // float4 of cell records per tile
 // FP64 force kernel shape.
 constexpr int kF64NT = 128;
@@ -84,6 +86,8 @@ struct Dev {
                                            // [2] warp-tiles [3] near warp-tiles
   int64_t* t_end = nullptr;      // 1
   int32_t* work_ctr = nullptr;   // next work item of the force kernels (zeroed by the plan)
+  int32_t* tune = nullptr;       // autotune table: (variant, B) per ceil(log2 m), kTuneBuckets
+  int32_t* sel = nullptr;        // the plan's choice from it: variant, targets per work item
   // 6th-order Hermite (order == 6; null otherwise): snap and crackle per
   // particle (dbl4, w unused), the new snap per active slot, and the
   // predicted accelerations of the sources (mixed: groups of 4 slots, 3 float4
@@ -129,6 +133,12 @@ struct ForceArgs {
   // j-partition: the sum runs over piece `part` of `parts` of every
   // cluster's sources (src_piece); parts <= 1: all sources
   int32_t part, parts;
+  // block steps with an autotune table: the plan writes the shape it chose
+  // for the step's active count (sel[0]: variant, sel[1]: its targets per
+  // work item); a force kernel launched as variant my_variant exits at once
+  // when it is not the chosen one, and the reduction takes sel[1] as NI
+  const int32_t* sel;       // nullptr: no selection (the launch is the chosen shape)
+  int32_t my_variant;
 };
 
 // ---------------------------------------------------------------- helpers

@@ -18,7 +18,9 @@ from . import build as _build
 
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ETIMEOUT, NB_ENONFINITE, NB_ESTATE = range(7)
 NB_FP64, NB_MIXED, NB_DS, NB_FP32 = 0, 1, 2, 3
-MIXED_VARIANTS = 6    # NB_MIXED_VARIANTS: shapes of the mixed force kernel
+MIXED_VARIANTS = 8    # NB_MIXED_VARIANTS: shapes of the mixed force kernel
+TUNE_BUCKETS = 32     # NB_TUNE_BUCKETS: autotune table entries (ceil(log2 m))
+TUNE_POINTS = 8       # NB_TUNE_POINTS: active counts the autotuner measures
 DEFAULT_VARIANT = 0   # the shape nb_default_config selects
 
 FUNCTIONS = [
@@ -29,7 +31,7 @@ FUNCTIONS = [
     "nb_energies", "nb_autotune", "nb_step_leapfrog", "nb_check_wait_timeout",
     "nb_noalloc_status", "nb_measure_rate", "nb_force_snap", "nb_correct_snap",
     "nb_get_derivs", "nb_set_derivs", "nb_source_piece", "nb_source_order", "nb_force_range",
-    "nb_block_force", "nb_block_correct", "nb_resort_sources",
+    "nb_block_force", "nb_block_correct", "nb_resort_sources", "nb_tune_table",
 ]
 PIECE_ALIGN = 128     # NB_PIECE_ALIGN: slots per tile of a source piece
 
@@ -83,7 +85,8 @@ def _load() -> ctypes.CDLL:
         "nb_profile_read": (ctypes.c_int, [P, P, P]),
         "nb_tile_stats": (ctypes.c_int, [P, P, P]),
         "nb_energies": (ctypes.c_int, [P, P, P]),
-        "nb_autotune": (ctypes.c_int, [P, P, P]),
+        "nb_autotune": (ctypes.c_int, [P, ctypes.c_char_p, P, P]),
+        "nb_tune_table": (ctypes.c_int, [P, P, P]),
         "nb_force_noalloc": (ctypes.c_int, [P, P, P, i64, P, i64, ctypes.c_double,
                                             ctypes.c_double, i32, P, P, P, P]),
         "nb_noalloc_status": (ctypes.c_int, [P]),
@@ -371,14 +374,25 @@ class Sim:
         _check(lib.nb_energies(self._ctx, _hptr(ek), _hptr(ep)), "nb_energies")
         return ek, ep
 
-    def autotune(self):
-        """Pick the fastest mixed kernel shape for this context; returns
-        (variant, {variant: [ms at fraction 1, 1/16, 1/256]})."""
+    def autotune(self, cache_path: str | None = None):
+        """The autotune table of (shape, i-split) per ceil(log2 m), measured
+        on this context or loaded from ``cache_path`` (nb_autotune); returns
+        (shape of the largest bucket, {variant: [ms at m = every 4^k-th
+        slot, k = 0 ..]}, all zero when the table came from the cache)."""
         v = ctypes.c_int32()
-        ms = np.zeros(3 * MIXED_VARIANTS)
-        _check(lib.nb_autotune(self._ctx, ctypes.byref(v), _hptr(ms)), "nb_autotune")
+        ms = np.zeros(TUNE_POINTS * MIXED_VARIANTS)
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(lib.nb_autotune(self._ctx, path, ctypes.byref(v), _hptr(ms)), "nb_autotune")
         self.cfg.variant = v.value
-        return v.value, {k: ms[3 * k:3 * k + 3].tolist() for k in range(MIXED_VARIANTS)}
+        ms = ms.reshape(TUNE_POINTS, MIXED_VARIANTS)
+        return v.value, {k: ms[:, k].tolist() for k in range(MIXED_VARIANTS)}
+
+    def tune_table(self):
+        """(shape, B) per ceil(log2 m) bucket: two int32 arrays (nb_tune_table)."""
+        v = np.empty(TUNE_BUCKETS, dtype=np.int32)
+        b = np.empty(TUNE_BUCKETS, dtype=np.int32)
+        _check(lib.nb_tune_table(self._ctx, _hptr(v), _hptr(b)), "nb_tune_table")
+        return v, b
 
     def get_state(self):
         n = self.n
