@@ -88,6 +88,9 @@ def parse():
                    help="step: the headline line; batch / drift / binaries: the other "
                         "configurations (their own JSON lines)")
     p.add_argument("--clusters", type=int, default=512)
+    p.add_argument("--rerun-worst", type=int, default=0,
+                   help="batch: re-run the K clusters of largest drift alone (mixed, FP64, "
+                        "FP64 with eta/4, FP64 with level_min 6)")
     p.add_argument("--t-end", type=float, default=None)
     p.add_argument("--max-seconds", type=float, default=600.0,
                    help="drift / binaries: wall-time bound of each integration")
@@ -168,7 +171,8 @@ def workload_batch(args):
     secs, steps, _ = integrate(sim, t_end)
     st = sim.stats()
     e1 = np.add(*sim.energies())
-    drift = np.abs(e1 / e0 - 1)
+    drift_signed = (e1 - e0) / np.abs(e0)
+    drift = np.abs(drift_signed)
     assert sim.status() == nbody.NB_OK
     out.update({"value": st.interactions / secs, "seconds": secs, "interactions": st.interactions,
                 "block_steps": st.block_steps,
@@ -186,6 +190,29 @@ def workload_batch(args):
     out["nongraph_seconds"] = secs2
     out["force_launches"] = nlaunch
     sim.close()
+    # 3) the clusters of largest drift, each integrated alone: the mixed path
+    # against FP64 (whose drift is the integrator's), and FP64 with shorter
+    # steps (eta and eta_start / 4; the largest step 2^-6 instead of 2^-3)
+    if args.rerun_worst > 0:
+        worst = []
+        for k in np.argsort(-drift)[:args.rerun_worst]:
+            o0, o1 = int(cl.offsets[k]), int(cl.offsets[k + 1])
+            row = {"cluster": int(k), "N": o1 - o0, "batch_drift": float(drift_signed[k])}
+            for name, prec, extra in (
+                    ("alone_mixed", nbody.NB_MIXED, {}), ("alone_fp64", nbody.NB_FP64, {}),
+                    ("fp64_eta_and_start_div4", nbody.NB_FP64, {"eta": 0.0025,
+                                                                "eta_start": 0.0025}),
+                    ("fp64_level_min_6", nbody.NB_FP64, {"level_min": 6})):
+                cfg = dict(eps=1e-4, precision=prec, level_min=3, graph_steps=16)
+                cfg.update(extra)
+                s1 = nbody.Sim(cl.pos[o0:o1], cl.vel[o0:o1], cl.mass[o0:o1], **cfg)
+                a0 = sum(s1.energy())
+                integrate(s1, t_end)
+                row[name] = (sum(s1.energy()) - a0) / abs(a0)
+                assert s1.status() == nbody.NB_OK
+                s1.close()
+            worst.append(row)
+        out["worst_clusters_alone"] = worst
     print(json.dumps(out), flush=True)
     return 0
 

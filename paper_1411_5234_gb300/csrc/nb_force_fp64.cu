@@ -140,6 +140,8 @@ __device__ __forceinline__ void issue64(dbl4* stp, dbl4* stv, dbl4* sta, uint64_
 
 template <int MODE>
 __global__ void __launch_bounds__(NT) k_force_fp64(const ForceArgs a) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   __shared__ __align__(128) dbl4 sp[2][JT];
   __shared__ __align__(128) dbl4 sv[2][JT];
   __shared__ __align__(128) dbl4 sa[2][MODE == kF64Snap ? JT : 1];
@@ -300,12 +302,10 @@ drain:
 
 cudaError_t launch_force_fp64(const ForceArgs& a, int grid, int mode, cudaStream_t st) {
   if (mode == kF64PotOnly)
-    k_force_fp64<kF64PotOnly><<<grid, NT, 0, st>>>(a);
-  else if (mode == kF64Snap)
-    k_force_fp64<kF64Snap><<<grid, NT, 0, st>>>(a);
-  else
-    k_force_fp64<kF64Full><<<grid, NT, 0, st>>>(a);
-  return cudaGetLastError();
+    return launch_chain(k_force_fp64<kF64PotOnly>, dim3(grid), dim3(NT), 0, st, a);
+  if (mode == kF64Snap)
+    return launch_chain(k_force_fp64<kF64Snap>, dim3(grid), dim3(NT), 0, st, a);
+  return launch_chain(k_force_fp64<kF64Full>, dim3(grid), dim3(NT), 0, st, a);
 }
 
 int force_fp64_ctas_per_sm() {

@@ -43,8 +43,7 @@ template <bool POT> using SF = mixk::MixShape<64, 4, POT, false, true, 1, 4, tru
 
 template <class Sh>
 cudaError_t launch_shape(const ForceArgs& a, int grid, cudaStream_t st) {
-  mixk::k_force_mixed<Sh><<<grid, Sh::NT, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_chain(mixk::k_force_mixed<Sh>, dim3(grid), dim3(Sh::NT), 0, st, a);
 }
 
 template <class Sh>

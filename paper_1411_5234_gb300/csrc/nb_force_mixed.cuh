@@ -446,6 +446,8 @@ __device__ __forceinline__ void issue_tile(float4* stage, float4* rec, float4* s
 
 template <class Sh>
 __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArgs a) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   constexpr int NT = Sh::NT, IPT = Sh::IPT, NI = Sh::NI;
   constexpr int SJ = Sh::ST * JT;  // sources per pipeline stage
   // a block step launches every shape of its autotune table; only the one

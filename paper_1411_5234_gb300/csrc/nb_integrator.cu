@@ -117,6 +117,8 @@ __global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
 
 // Next block time of every cluster whose time is below the end time.
 __global__ void k_tmin(Dev d, int T) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   __shared__ long long sh[32];
   const int64_t i0 = blockIdx.x * (int64_t)blockDim.x;
   const int64_t i = i0 + threadIdx.x;
@@ -166,6 +168,8 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
                                                           int64_t t_fixed, int T, int write_mix,
                                                           int write64, int count_due,
                                                           int zero_tau) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   __shared__ float shd[kMixJT / 32];
   __shared__ int32_t shi[32];
   const int32_t tile = blockIdx.x;
@@ -221,6 +225,8 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
 // Active list in source-slot order (spatially sorted targets), plus each
 // cluster's offset in it; one CTA per source tile as in k_predict_tiles.
 __global__ void __launch_bounds__(kMixJT) k_scatter_tiles(Dev d, int T) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   __shared__ int32_t sh[32];
   const int32_t tile = blockIdx.x;
   const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
@@ -364,13 +370,19 @@ __device__ __forceinline__ void plan_body(const Dev& d, const PlanArgs& p0, bool
   }
 }
 
-__global__ void k_plan(Dev d, PlanArgs p) { plan_body(d, p, true); }
+__global__ void k_plan(Dev d, PlanArgs p) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
+  plan_body(d, p, true);
+}
 
 // Block step: the scan of the per-tile due counts (k_scan), each cluster's
 // offset in the active list (the scanned count of its first tile) and the
 // plan, in one CTA of 1024 threads.  t_min stays for k_scatter_tiles; the
 // corrector resets it.
 __global__ void k_scan_plan(Dev d, int32_t nblk, PlanArgs p) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   __shared__ int32_t sh[32];
   int32_t carry = 0;
   for (int32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
@@ -422,6 +434,8 @@ constexpr size_t kWideSmem = sizeof(double) * kPartialCompsSnap * kWideRows * 32
 template <int C>
 __global__ void __launch_bounds__(32 * kWideRows) k_reduce(ForceArgs a, int NI,
                                                            int with_acc) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   extern __shared__ double red[];  // [component][row r][lane]
   __shared__ int last_sh;
   const int32_t K = a.K;
@@ -583,6 +597,8 @@ __device__ __forceinline__ int32_t new_level(double dt, int32_t L_old, int64_t t
 // the square root of norm q.  The per-lane FP64 work is about a third of a
 // particle's (GB300's FP64 pipe is the bound here).
 __global__ void k_correct(Dev d, CorrectArgs c) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   const int64_t m = c.count_dev ? (int64_t)*c.count_dev : c.count_host;
   if (c.reset_tmin && blockIdx.x == 0)  // the block step's t_min is used up
     for (int32_t k = threadIdx.x; k < d.K; k += blockDim.x) d.t_min[k] = LLONG_MAX;
@@ -685,6 +701,8 @@ __global__ void k_correct(Dev d, CorrectArgs c) {
 // the end of the step; the power-of-two level follows the 4th-order rules.
 // The crackle is kept for the next prediction.
 __global__ void k_correct6(Dev d, CorrectArgs c) {
+  pdl_wait();  // the previous kernel of the chain has completed
+  pdl_launch();
   const int64_t m = c.count_dev ? (int64_t)*c.count_dev : c.count_host;
   if (c.reset_tmin && blockIdx.x == 0)  // the block step's t_min is used up
     for (int32_t k = threadIdx.x; k < d.K; k += blockDim.x) d.t_min[k] = LLONG_MAX;
@@ -958,14 +976,14 @@ cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_tmin(const Dev& d, int T, cudaStream_t st) {
-  k_tmin<<<static_cast<int>(ceil_div64(d.N, 256)), 256, 0, st>>>(d, T);
-  return cudaGetLastError();
+  return launch_chain(k_tmin, dim3(static_cast<unsigned>(ceil_div64(d.N, 256))), dim3(256), 0,
+                      st, d, T);
 }
 cudaError_t launch_predict(const Dev& d, const int64_t* t_tgt, int64_t t_fixed, int T,
                            bool mix, bool f64, bool count_due, cudaStream_t st, bool zero_tau) {
-  k_predict_tiles<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d, t_tgt, t_fixed, T, mix,
-                                                                  f64, count_due, zero_tau);
-  return cudaGetLastError();
+  return launch_chain(k_predict_tiles, dim3(static_cast<unsigned>(d.n_tiles)), dim3(kMixJT), 0,
+                      st, d, t_tgt, t_fixed, T, mix ? 1 : 0, f64 ? 1 : 0, count_due ? 1 : 0,
+                      zero_tau ? 1 : 0);
 }
 cudaError_t launch_wait_probe(uint32_t* status, long long budget, cudaStream_t st) {
   k_wait_probe<<<1, 32, 0, st>>>(status, budget);
@@ -981,13 +999,14 @@ cudaError_t launch_leapfrog(const Dev& d, const double* a_new, double h, double 
   return cudaGetLastError();
 }
 cudaError_t launch_scan_plan_scatter(const Dev& d, const PlanArgs& p, int T, cudaStream_t st) {
-  k_scan_plan<<<1, 1024, 0, st>>>(d, static_cast<int32_t>(d.n_tiles), p);
-  k_scatter_tiles<<<static_cast<int>(d.n_tiles), kMixJT, 0, st>>>(d, T);
-  return cudaGetLastError();
+  cudaError_t e = launch_chain(k_scan_plan, dim3(1), dim3(1024), 0, st, d,
+                               static_cast<int32_t>(d.n_tiles), p);
+  if (e != cudaSuccess) return e;
+  return launch_chain(k_scatter_tiles, dim3(static_cast<unsigned>(d.n_tiles)), dim3(kMixJT), 0,
+                      st, d, T);
 }
 cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
-  k_plan<<<1, 512, 0, st>>>(d, p);
-  return cudaGetLastError();
+  return launch_chain(k_plan, dim3(1), dim3(512), 0, st, d, p);
 }
 cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_bound,
                           int grid, cudaStream_t st) {
@@ -996,10 +1015,10 @@ cudaError_t launch_reduce(const ForceArgs& a, int NI, bool with_acc, int64_t m_b
   (void)m_bound;
   const int g = grid > 0 ? grid : 1;
   if (a.comps == kPartialCompsSnap)
-    k_reduce<kPartialCompsSnap><<<g, 32 * kWideRows, kWideSmem, st>>>(a, NI, with_acc ? 1 : 0);
-  else
-    k_reduce<kPartialComps><<<g, 32 * kWideRows, kWideSmem, st>>>(a, NI, with_acc ? 1 : 0);
-  return cudaGetLastError();
+    return launch_chain(k_reduce<kPartialCompsSnap>, dim3(g), dim3(32 * kWideRows), kWideSmem, st,
+                        a, NI, with_acc ? 1 : 0);
+  return launch_chain(k_reduce<kPartialComps>, dim3(g), dim3(32 * kWideRows), kWideSmem, st, a,
+                      NI, with_acc ? 1 : 0);
 }
 cudaError_t integrator_setup() {
   cudaError_t e = cudaFuncSetAttribute(k_reduce<kPartialComps>,
@@ -1013,15 +1032,13 @@ cudaError_t integrator_setup() {
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {
   // 4 lanes per particle in 32-thread CTAs: a few hundred active particles
   // still spread over many SMs (FP64 arithmetic, ~2 lanes per SM per clock)
-  k_correct<<<blocks_for(4 * m_bound, 32), 32, 0, st>>>(d, c);
-  return cudaGetLastError();
+  return launch_chain(k_correct, dim3(blocks_for(4 * m_bound, 32)), dim3(32), 0, st, d, c);
 }
 cudaError_t launch_correct6(const Dev& d, const CorrectArgs& c, int64_t m_bound,
                             cudaStream_t st) {
   // one thread per particle in 32-thread CTAs: few active particles still
   // spread over many SMs (FP64 arithmetic)
-  k_correct6<<<blocks_for(m_bound, 32), 32, 0, st>>>(d, c);
-  return cudaGetLastError();
+  return launch_chain(k_correct6, dim3(blocks_for(m_bound, 32)), dim3(32), 0, st, d, c);
 }
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,
                                cudaStream_t st) {

@@ -19,6 +19,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 // 32-byte aligned double vector (CUDA 13 names the alignment explicitly).
@@ -142,6 +143,37 @@ struct ForceArgs {
 };
 
 // ---------------------------------------------------------------- helpers
+
+// Programmatic dependent launch.  The kernels of a block step (t_next,
+// predictor, scan and plan, scatter, force, reduction, corrector) run one
+// after the other, and with few active particles each takes a few
+// microseconds, about as long as a launch.  Launched with launch_chain, the
+// next kernel of the chain is put on the GPU while the current one runs:
+// every chain kernel first waits until the kernel before it has completed
+// and its writes are visible (pdl_wait, which is why each of them, even one
+// that exits at once, waits before anything else: the wait is what carries
+// the ordering down the chain), then allows the kernel after it to launch
+// (pdl_launch).  Outside a programmatic launch both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
