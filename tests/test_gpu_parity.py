@@ -502,6 +502,16 @@ def test_block_steps_with_a_table_of_several_shapes(nb, tmp_path):
     assert sim.status() == nb.NB_OK
     sim.close()
     assert len({7 if b <= 6 else 6 if b <= 9 else 3 if b <= 11 else 0 for b in m_seen}) >= 2
+    # the same steps captured in graphs of 8 (the plan picks the shape on the
+    # device inside the graph) give the same state as the direct launches
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, **kw)
+    sim.autotune(str(cache))
+    sim.step(64)
+    s_graph = sim.get_state()
+    assert sim.status() == nb.NB_OK
+    sim.close()
+    for key in ("pos", "vel", "t", "level"):
+        assert np.array_equal(s_graph[key], s[key]), key
     assert np.array_equal(s["t"], s_ref["t"])
     ex = np.linalg.norm(s["pos"] - s_ref["pos"], axis=1) / np.linalg.norm(s_ref["pos"], axis=1)
     assert ex.max() < 1e-9, ex.max()
