@@ -83,6 +83,8 @@ def parse():
                    help="run only nb_force on m random targets of N (profiling case)")
     p.add_argument("--m", type=int, default=16384)
     p.add_argument("--variant", type=int, default=None, help="mixed force kernel shape")
+    p.add_argument("--bfactor", type=int, default=0,
+                   help="i-split factor B of the headline step (0: the plan's or the table's)")
     p.add_argument("--workload", default="step",
                    choices=["step", "batch", "drift", "binaries", "leapfrog", "hermite6"],
                    help="step: the headline line; batch / drift / binaries: the other "
@@ -669,6 +671,8 @@ def main():
     cl = make_cluster(n, seed=rank)
     L = args.level
     kw = {} if args.variant is None else {"variant": args.variant}
+    if args.bfactor > 0:
+        kw["bfactor"] = args.bfactor
     sim = nbody.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nbody.NB_MIXED,
                     level_min=L, level_max=L, graph_steps=0, **kw)
     stream = sim.stream
