@@ -145,6 +145,16 @@ def integrate(sim, t_end, chunk=512, max_seconds=None, near=None, resort_factor=
     return ev0.elapsed_time(ev1) * 1e-3, steps, sim.time(st.t_min)
 
 
+def per_kernel_shares(kinds, seconds, steps):
+    """Per kind of launch: device microseconds per block step and share of
+    the run's device time (direct launches with events); "gaps" is the rest:
+    time between the launches."""
+    out = {k: {"us_per_step": ms * 1e3 / max(steps, 1), "share": ms * 1e-3 / seconds,
+               "launches": n} for k, (ms, n) in kinds.items()}
+    out["gaps"] = {"share": 1.0 - sum(v["share"] for v in out.values())}
+    return out
+
+
 def workload_batch(args):
     """Independent Plummer clusters of log-uniform size in one context: every
     block step advances every cluster; CUDA-graph-captured step sequences."""
@@ -186,8 +196,10 @@ def workload_batch(args):
     if args.variant is None and not args.no_tune:
         sim.autotune(cache)   # the same table, from the cache
     sim.profile(True)
+    sim.profile_kernels()
     secs2, _, _ = integrate(sim, t_end)
     fms, nlaunch = sim.profile_read()
+    out["per_kernel"] = per_kernel_shares(sim.profile_kernels(), secs2, sim.stats().block_steps)
     out["force_kernel_share"] = fms * 1e-3 / secs2
     out["nongraph_seconds"] = secs2
     out["force_launches"] = nlaunch
@@ -273,14 +285,17 @@ def workload_drift(args):
             if not args.no_tune:
                 sim.autotune()
             sim.profile(True)
+            sim.profile_kernels()
             secs2, _, _ = integrate(sim, min(t_end, 0.125), max_seconds=args.max_seconds)
             fms, nlaunch = sim.profile_read()
+            kinds = sim.profile_kernels()
             assert sim.status() == nbody.NB_OK
             nsteps = sim.stats().block_steps
             out[name]["force_kernel_share"] = {
                 "share": fms * 1e-3 / secs2, "t_end": min(t_end, 0.125),
                 "block_steps": nsteps, "force_launches": nlaunch,
                 "us_per_step": secs2 / max(nsteps, 1) * 1e6}
+            out[name]["per_kernel"] = per_kernel_shares(kinds, secs2, nsteps)
             sim.close()
     base = out.get("fp64", {}).get("energy_drift")
     comp = out.get("mixed_at_fp64_n", out["mixed"])["energy_drift"]

@@ -341,6 +341,16 @@ int nb_stats(nb_ctx *ctx, int64_t *block_steps, int64_t *interactions,
 int nb_profile_enable(nb_ctx *ctx, int enable);
 int nb_profile_read(nb_ctx *ctx, double *force_ms, int64_t *launches);
 
+/* The same timing for every kind of launch of a block step (and of
+ * nb_force): host arrays of NB_PROFILE_KINDS entries (either may be NULL),
+ * in this order: next block time, predictor, active list and plan (scan,
+ * plan and scatter, or the plan alone), force kernel, i-split reduction,
+ * corrector.  Summed device milliseconds and launch counts since the
+ * previous nb_profile_kernels (a count apart from nb_profile_read's).  The
+ * sum over kinds leaves out the gaps between launches.  Synchronises. */
+#define NB_PROFILE_KINDS 6
+int nb_profile_kernels(nb_ctx *ctx, double *ms_by_kind, int64_t *launches_by_kind);
+
 /* Mixed force kernel diagnostics since nb_init (host outputs, either may be
  * NULL): source cells (64 slots each) processed by a warp, and how many of
  * those took the near (full double-single) path because some target of the

@@ -33,6 +33,9 @@ struct NvtxRange {
 
 constexpr size_t kAlign = 256;
 constexpr int kEnergyBlocks = 304;
+// kinds of timed launches (nb_profile_kernels, in this order)
+enum { kProfTnext = 0, kProfPredict, kProfPlan, kProfForce, kProfReduce, kProfCorrect };
+static_assert(kProfCorrect + 1 == NB_PROFILE_KINDS, "the kinds the ABI announces");
 
 struct Layout {
   size_t snap, crackle, snap_new, src_acc_mix, src64_acc;  // 6th order only (else empty)
@@ -221,12 +224,17 @@ struct nb_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
   bool graph_broken = false;
-  // force-kernel timing (nb_profile_enable)
+  // kernel timing (nb_profile_enable): event pairs around the launches of
+  // each kind (kProf*), summed per kind; the force kind also feeds
+  // nb_profile_read's own total
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  std::vector<int> ev_kind;
   double prof_ms = 0.0;
   int64_t prof_launches = 0;
+  double kind_ms[NB_PROFILE_KINDS] = {};
+  int64_t kind_n[NB_PROFILE_KINDS] = {};
   // j-partition: the piece of every cluster's sources the force launches of
   // the current call sum over (parts <= 1: all sources; set by PieceScope)
   int32_t part = 0, parts = 1;
@@ -370,12 +378,18 @@ cudaError_t prof_collect(nb_ctx* c, bool all) {
     float ms = 0.f;
     cudaError_t e = cudaEventElapsedTime(&ms, p.first, p.second);
     if (e != cudaSuccess) return e;
-    c->prof_ms += ms;
-    c->prof_launches += 1;
+    const int kind = c->ev_kind[k];
+    c->kind_ms[kind] += ms;
+    c->kind_n[kind] += 1;
+    if (kind == kProfForce) {
+      c->prof_ms += ms;
+      c->prof_launches += 1;
+    }
     c->ev_free.push_back(p.first);
     c->ev_free.push_back(p.second);
   }
   c->ev_pending.erase(c->ev_pending.begin(), c->ev_pending.begin() + k);
+  c->ev_kind.erase(c->ev_kind.begin(), c->ev_kind.begin() + k);
   return cudaSuccess;
 }
 
@@ -395,6 +409,23 @@ cudaError_t prof_events(nb_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
     }
   }
   *ev = {x[0], x[1]};
+  return cudaSuccess;
+}
+
+// Profiling only (c->prof): an event before and after the launches of one
+// kind; nothing otherwise.
+cudaError_t prof_begin(nb_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
+  if (!c->prof) return cudaSuccess;
+  cudaError_t e = prof_events(c, ev);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(ev->first, c->st);
+}
+cudaError_t prof_end(nb_ctx* c, const std::pair<cudaEvent_t, cudaEvent_t>& ev, int kind) {
+  if (!c->prof) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(ev.second, c->st);
+  if (e != cudaSuccess) return e;
+  c->ev_pending.push_back(ev);
+  c->ev_kind.push_back(kind);
   return cudaSuccess;
 }
 
@@ -419,9 +450,14 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
   }
   const bool device_select = tabled && m_host < 0;
   if (!planned) {
-    e = launch_plan(c->d, plan_args(c, f64, step_mode, count, acc_only, false, variant, forced_b,
-                                    device_select),
-                    c->st);
+    std::pair<cudaEvent_t, cudaEvent_t> pev{nullptr, nullptr};
+    e = prof_begin(c, &pev);
+    if (e == cudaSuccess)
+      e = launch_plan(c->d,
+                      plan_args(c, f64, step_mode, count, acc_only, false, variant, forced_b,
+                                device_select),
+                      c->st);
+    if (e == cudaSuccess) e = prof_end(c, pev, kProfPlan);
     if (e != cudaSuccess) return e;
   }
   ForceArgs fa = force_args(c, active, rows, acc, sa, jerk, sj, pot, sp, f64);
@@ -459,9 +495,13 @@ cudaError_t enqueue_force(nb_ctx* c, const int32_t* active, const int32_t* rows,
     e = cudaEventRecord(ev.second, c->st);
     if (e != cudaSuccess) return e;
     c->ev_pending.push_back(ev);
+    c->ev_kind.push_back(kProfForce);
   }
   const int ni = f64 ? kF64NI : acc_only ? force_mixed_acc_ni() : force_mixed_ni(variant);
-  return launch_reduce(fa, ni, !pot_only, m_bound, c->sms, c->st);
+  std::pair<cudaEvent_t, cudaEvent_t> rev{nullptr, nullptr};
+  e = prof_begin(c, &rev);
+  if (e == cudaSuccess) e = launch_reduce(fa, ni, !pot_only, m_bound, c->sms, c->st);
+  return e != cudaSuccess ? e : prof_end(c, rev, kProfReduce);
 }
 
 // plan + force with snap + partial reduce (the 6th-order scheme's force; the
@@ -499,9 +539,13 @@ cudaError_t enqueue_force_snap(nb_ctx* c, const int32_t* active, const int32_t* 
     e = cudaEventRecord(ev.second, c->st);
     if (e != cudaSuccess) return e;
     c->ev_pending.push_back(ev);
+    c->ev_kind.push_back(kProfForce);
   }
   const int ni = f64 ? kF64NI : force_mixed_snap_ni();
-  return launch_reduce(fa, ni, true, m_bound, c->sms, c->st);
+  std::pair<cudaEvent_t, cudaEvent_t> rev{nullptr, nullptr};
+  e = prof_begin(c, &rev);
+  if (e == cudaSuccess) e = launch_reduce(fa, ni, true, m_bound, c->sms, c->st);
+  return e != cudaSuccess ? e : prof_end(c, rev, kProfReduce);
 }
 
 // First half of a block step: the next block time, the prediction, the
@@ -510,13 +554,21 @@ cudaError_t enqueue_force_snap(nb_ctx* c, const int32_t* active, const int32_t* 
 cudaError_t enqueue_block_force(nb_ctx* c) {
   const int T = c->cfg.tick_exp;
   const bool f64 = !is_mixed(c);
-  cudaError_t e = launch_tmin(c->d, T, c->st);
-  if (e != cudaSuccess) return e;
-  e = launch_predict(c->d, c->d.t_min, 0, T, !f64, f64, true, c->st);
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  cudaError_t e = prof_begin(c, &ev);
+  if (e == cudaSuccess) e = launch_tmin(c->d, T, c->st);
+  if (e == cudaSuccess) e = prof_end(c, ev, kProfTnext);
+  if (e == cudaSuccess) e = prof_begin(c, &ev);
+  if (e == cudaSuccess) e = launch_predict(c->d, c->d.t_min, 0, T, !f64, f64, true, c->st);
+  if (e == cudaSuccess) e = prof_end(c, ev, kProfPredict);
   if (e != cudaSuccess) return e;
   const bool o6 = c->cfg.order == 6;
-  e = launch_scan_plan_scatter(
-      c->d, plan_args(c, f64, 1, 1, false, o6, -1, -1, uses_table(c, f64, false, o6)), T, c->st);
+  e = prof_begin(c, &ev);
+  if (e == cudaSuccess)
+    e = launch_scan_plan_scatter(
+        c->d, plan_args(c, f64, 1, 1, false, o6, -1, -1, uses_table(c, f64, false, o6)), T,
+        c->st);
+  if (e == cudaSuccess) e = prof_end(c, ev, kProfPlan);
   if (e != cudaSuccess) return e;
   double* an = reinterpret_cast<double*>(c->d.acc_new);
   double* jn = reinterpret_cast<double*>(c->d.jerk_new);
@@ -547,12 +599,17 @@ cudaError_t enqueue_block_correct(nb_ctx* c) {
   ca.lmin = c->cfg.level_min;
   ca.lmax = c->cfg.level_max;
   ca.reset_tmin = 1;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  cudaError_t e = prof_begin(c, &ev);
+  if (e != cudaSuccess) return e;
   if (c->cfg.order == 6) {
     ca.snap = reinterpret_cast<double*>(c->d.snap_new);
     ca.ss = 4;
-    return launch_correct6(c->d, ca, c->d.N, c->st);
+    e = launch_correct6(c->d, ca, c->d.N, c->st);
+  } else {
+    e = launch_correct(c->d, ca, c->d.N, c->st);
   }
-  return launch_correct(c->d, ca, c->d.N, c->st);
+  return e != cudaSuccess ? e : prof_end(c, ev, kProfCorrect);
 }
 
 cudaError_t enqueue_block_step(nb_ctx* c) {
@@ -1327,6 +1384,18 @@ int nb_profile_read(nb_ctx* c, double* force_ms, int64_t* launches) {
   if (launches) *launches = c->prof_launches;
   c->prof_ms = 0.0;
   c->prof_launches = 0;
+  return NB_OK;
+}
+
+int nb_profile_kernels(nb_ctx* c, double* ms_by_kind, int64_t* launches_by_kind) {
+  if (!c) return NB_EINVAL;
+  NB_TRY(prof_collect(c, true));
+  for (int k = 0; k < NB_PROFILE_KINDS; ++k) {
+    if (ms_by_kind) ms_by_kind[k] = c->kind_ms[k];
+    if (launches_by_kind) launches_by_kind[k] = c->kind_n[k];
+    c->kind_ms[k] = 0.0;
+    c->kind_n[k] = 0;
+  }
   return NB_OK;
 }
 

@@ -31,8 +31,10 @@ FUNCTIONS = [
     "nb_energies", "nb_autotune", "nb_step_leapfrog", "nb_check_wait_timeout",
     "nb_noalloc_status", "nb_measure_rate", "nb_force_snap", "nb_correct_snap",
     "nb_get_derivs", "nb_set_derivs", "nb_source_piece", "nb_source_order", "nb_force_range",
-    "nb_block_force", "nb_block_correct", "nb_resort_sources", "nb_tune_table",
+    "nb_block_force", "nb_block_correct", "nb_resort_sources", "nb_tune_table", "nb_profile_kernels",
 ]
+PROFILE_KINDS = ("t_next", "predictor", "active_list_and_plan", "force", "reduction",
+                 "corrector")   # NB_PROFILE_KINDS, in the ABI's order
 PIECE_ALIGN = 128     # NB_PIECE_ALIGN: slots per tile of a source piece
 
 
@@ -87,6 +89,7 @@ def _load() -> ctypes.CDLL:
         "nb_energies": (ctypes.c_int, [P, P, P]),
         "nb_autotune": (ctypes.c_int, [P, ctypes.c_char_p, P, P]),
         "nb_tune_table": (ctypes.c_int, [P, P, P]),
+        "nb_profile_kernels": (ctypes.c_int, [P, P, P]),
         "nb_force_noalloc": (ctypes.c_int, [P, P, P, i64, P, i64, ctypes.c_double,
                                             ctypes.c_double, i32, P, P, P, P]),
         "nb_noalloc_status": (ctypes.c_int, [P]),
@@ -386,6 +389,14 @@ class Sim:
         self.cfg.variant = v.value
         ms = ms.reshape(TUNE_POINTS, MIXED_VARIANTS)
         return v.value, {k: ms[:, k].tolist() for k in range(MIXED_VARIANTS)}
+
+    def profile_kernels(self):
+        """{kind: (device ms, launches)} of every kind of launch since the
+        previous call, while profiling is on (nb_profile_kernels)."""
+        ms = np.zeros(len(PROFILE_KINDS))
+        n = np.zeros(len(PROFILE_KINDS), dtype=np.int64)
+        _check(lib.nb_profile_kernels(self._ctx, _hptr(ms), _hptr(n)), "nb_profile_kernels")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROFILE_KINDS)}
 
     def tune_table(self):
         """(shape, B) per ceil(log2 m) bucket: two int32 arrays (nb_tune_table)."""

@@ -696,3 +696,27 @@ def test_nonfinite_state_is_reported(nb, prec):
         assert sim.status() == nb.NB_ENONFINITE
     finally:
         sim.close()
+
+
+def test_profile_kernels_times_every_kind_of_launch(nb):
+    """nb_profile_kernels: with profiling on, each block step times one
+    launch of every kind (t_next, predictor, plan, force, reduction,
+    corrector); nb_profile_read keeps reporting the force alone."""
+    cl = inputs.plummer(4096, seed=46)
+    sim = nb.Sim(cl.pos, cl.vel, cl.mass, eps=1e-4, precision=nb.NB_MIXED, level_min=3,
+                 level_max=14, graph_steps=8)
+    sim.step(4)
+    sim.profile(True)
+    sim.profile_kernels()
+    sim.profile_read()
+    sim.step(12)
+    kinds = sim.profile_kernels()
+    fms, nf = sim.profile_read()
+    assert sim.status() == nb.NB_OK
+    assert list(kinds) == list(nb.PROFILE_KINDS)
+    for k, (ms, n) in kinds.items():
+        assert n == 12 and ms > 0, (k, ms, n)
+    assert nf == 12 and fms == pytest.approx(kinds["force"][0])
+    assert all(n == 0 for _, n in sim.profile_kernels().values())   # read resets
+    sim.profile(False)
+    sim.close()
