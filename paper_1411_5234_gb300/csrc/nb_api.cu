@@ -41,7 +41,8 @@ struct Layout {
   size_t snap, crackle, snap_new, src_acc_mix, src64_acc;  // 6th order only (else empty)
   size_t pos, vel, acc, jerk, acc_new, jerk_new, t, level, cid, active, src_mix, src64_pos,
       src64_vel, partials, blk_count, off, soff, t_cur, t_min, act_off, item_off, wt_off, wide_cnt, bfac, esum,
-      status, counters, t_end, work, tune, sel, tiles, toff, sperm, sinv, mark, rows, total;
+      status, counters, t_end, work, tune, sel, due_mask, tiles, toff, sperm, sinv, mark, rows,
+      total;
   int64_t S, part_items, n_tiles;
 };
 
@@ -92,6 +93,7 @@ Layout make_layout(int64_t N, int32_t K, int64_t S, int64_t n_tiles, int order) 
   L.work = take(c, 4);
   L.tune = take(c, 8 * (size_t)kTuneBuckets);
   L.sel = take(c, 8);
+  L.due_mask = take(c, 4 * (kMixJT / 32) * (size_t)n_tiles);
   L.tiles = take(c, 16 * kTileRecF4 * (size_t)n_tiles);
   L.toff = take(c, 4 * ((size_t)K + 1));
   L.sperm = take(c, 4 * (size_t)S);
@@ -815,6 +817,7 @@ int nb_init(nb_ctx** out, const nb_config* cfg, int32_t n_clusters, const int64_
   d.work_ctr = reinterpret_cast<int32_t*>(w + c->L.work);
   d.tune = reinterpret_cast<int32_t*>(w + c->L.tune);
   d.sel = reinterpret_cast<int32_t*>(w + c->L.sel);
+  d.due_mask = reinterpret_cast<uint32_t*>(w + c->L.due_mask);
   d.order = cfg->order;
   if (cfg->order == 6) {
     d.snap = reinterpret_cast<dbl4*>(w + c->L.snap);

@@ -142,20 +142,52 @@ __global__ void k_tmin(Dev d, int T) {
   }
 }
 
+// In-place exclusive scan of the n counts cnt[0 .. n) by one CTA of
+// blockDim.x <= kScanThreads threads; returns the total (in every thread).
+// Chunks of kScanPerThread counts per thread are staged in shared memory by
+// coalesced loads; each thread sums its consecutive counts, one block scan
+// gives its offset, and it writes its counts' prefixes back: one block scan
+// per chunk of blockDim.x * kScanPerThread counts instead of one per
+// blockDim.x.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 8;
+__device__ __forceinline__ int32_t scan_counts(int32_t* cnt, int32_t n, int32_t* sh,
+                                               int32_t* chunk) {
+  const int32_t per = blockDim.x * kScanPerThread;
+  const int32_t b0 = threadIdx.x * kScanPerThread;
+  int32_t carry = 0;
+  for (int32_t c0 = 0; c0 < n; c0 += per) {
+    const int32_t len = min(per, n - c0);
+    for (int32_t q = threadIdx.x; q < len; q += blockDim.x) chunk[q] = cnt[c0 + q];
+    __syncthreads();
+    int32_t local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) local += b0 + q < len ? chunk[b0 + q] : 0;
+    int32_t tot;
+    int32_t run = carry + block_excl_scan(local, sh, &tot);
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) {
+      if (b0 + q < len) {
+        const int32_t v = chunk[b0 + q];
+        chunk[b0 + q] = run;
+        run += v;
+      }
+    }
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q < len; q += blockDim.x) cnt[c0 + q] = chunk[q];
+    carry += tot;
+    __syncthreads();  // the chunk buffer is refilled next
+  }
+  return carry;
+}
+
 // Exclusive scan of nblk block counts (one CTA of 1024 threads); the total
 // goes to act_off[K].
-__global__ void k_scan(Dev d, int32_t nblk) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(Dev d, int32_t nblk) {
   __shared__ int32_t sh[32];
-  int32_t carry = 0;
-  for (int32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
-    const int32_t b = b0 + threadIdx.x;
-    const int32_t v = b < nblk ? d.blk_count[b] : 0;
-    int32_t tot;
-    const int32_t ex = block_excl_scan(v, sh, &tot);
-    if (b < nblk) d.blk_count[b] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) d.act_off[d.K] = carry;
+  __shared__ int32_t chunk[kScanThreads * kScanPerThread];
+  const int32_t total = scan_counts(d.blk_count, nblk, sh, chunk);
+  if (threadIdx.x == 0) d.act_off[d.K] = total;
 }
 
 // Predict the particles of one source tile (one CTA of kMixJT threads, one
@@ -179,7 +211,10 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
   const int32_t p = in ? d.sperm[s] : -1;
   const int64_t tn = t_tgt ? t_tgt[k] : t_fixed;
   if (tn == LLONG_MAX) {  // uniform over the CTA: the whole tile is one cluster
-    if (count_due && threadIdx.x == 0) d.blk_count[tile] = 0;
+    if (count_due) {
+      if (threadIdx.x == 0) d.blk_count[tile] = 0;
+      if ((threadIdx.x & 31) == 0) d.due_mask[tile * (kMixJT / 32) + (threadIdx.x >> 5)] = 0u;
+    }
     return;
   }
   int32_t due = 0;
@@ -199,6 +234,9 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
     m = P.w;
   }
   if (count_due) {
+    // the due slots as one bit per lane and warp, for k_scatter_tiles
+    const uint32_t bal = __ballot_sync(0xffffffffu, due != 0);
+    if ((threadIdx.x & 31) == 0) d.due_mask[tile * (kMixJT / 32) + (threadIdx.x >> 5)] = bal;
     const int32_t tot =
         block_reduce<int32_t>(due, [](int32_t x, int32_t y) { return x + y; }, shi, 0);
     if (threadIdx.x == 0) d.blk_count[tile] = tot;
@@ -222,25 +260,37 @@ __global__ void __launch_bounds__(kMixJT) k_predict_tiles(Dev d, const int64_t* 
   if (write_mix) build_mixed_tile(d.src_mix, d.tiles, tile, s, in, p >= 0, xp, m, vp, shd);
 }
 
-// Active list in source-slot order (spatially sorted targets), plus each
-// cluster's offset in it; one CTA per source tile as in k_predict_tiles.
-__global__ void __launch_bounds__(kMixJT) k_scatter_tiles(Dev d, int T) {
+// Active list in source-slot order (spatially sorted targets), from the
+// predictor's due bits and the scanned per-tile counts.
+constexpr int kScatterThreads = 256;
+__global__ void __launch_bounds__(kScatterThreads) k_scatter_tiles(Dev d, int T) {
   pdl_wait();  // the previous kernel of the chain has completed
   pdl_launch();
-  __shared__ int32_t sh[32];
-  const int32_t tile = blockIdx.x;
-  const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
-  const int64_t s = d.soff[k] + (int64_t)(tile - d.toff[k]) * kMixJT + threadIdx.x;
-  const bool in = s < d.soff[k + 1];
-  const int32_t p = in ? d.sperm[s] : -1;
-  const int64_t tn = d.t_min[k];
-  const int32_t f =
-      (p >= 0 && tn != LLONG_MAX && d.t[p] + step_ticks(d.level[p], T) == tn) ? 1 : 0;
-  int32_t tot;
-  const int32_t ex = block_excl_scan(f, sh, &tot);
-  const int32_t run = d.blk_count[tile];
-  if (f) d.active[run + ex] = p;
-  if (s == d.soff[k]) d.act_off[k] = run;
+  (void)T;
+  // one warp per word of the predictor's due bits (a tile has kMixJT / 32),
+  // a grid of a few CTAs per SM striding over them (a CTA per tile spends
+  // more on launching CTAs than on the work when few particles are due): a
+  // slot's place in the active list is its tile's offset (the scan) plus the
+  // due slots before it in the tile (population counts).  Words without due
+  // slots cost one load; the particle map is read for due slots only.  (Each
+  // cluster's offset in the list, act_off[k], was set by the scan.)
+  constexpr int kWords = kMixJT / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = d.n_tiles * kWords;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < nw;
+       gw += stride) {
+    const uint32_t mine = d.due_mask[gw];
+    if (!((mine >> lane) & 1u)) continue;
+    const int32_t tile = static_cast<int32_t>(gw / kWords);
+    const int w = static_cast<int>(gw - (int64_t)tile * kWords);
+    int32_t before = 0;
+    for (int q = 0; q < w; ++q) before += __popc(d.due_mask[(int64_t)tile * kWords + q]);
+    const int32_t ex = before + __popc(mine & ((1u << lane) - 1u));
+    const int32_t k = upper_bound_i32(d.toff, d.K + 1, tile) - 1;
+    const int64_t slot = d.soff[k] + (int64_t)(tile - d.toff[k]) * kMixJT + w * 32 + lane;
+    d.active[d.blk_count[tile] + ex] = d.sperm[slot];
+  }
 }
 
 // Work plan: per-cluster active count m_k, i-split factor B_k (Sec. 2 item 3)
@@ -380,20 +430,13 @@ __global__ void k_plan(Dev d, PlanArgs p) {
 // offset in the active list (the scanned count of its first tile) and the
 // plan, in one CTA of 1024 threads.  t_min stays for k_scatter_tiles; the
 // corrector resets it.
-__global__ void k_scan_plan(Dev d, int32_t nblk, PlanArgs p) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_plan(Dev d, int32_t nblk, PlanArgs p) {
   pdl_wait();  // the previous kernel of the chain has completed
   pdl_launch();
   __shared__ int32_t sh[32];
-  int32_t carry = 0;
-  for (int32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
-    const int32_t b = b0 + threadIdx.x;
-    const int32_t v = b < nblk ? d.blk_count[b] : 0;
-    int32_t tot;
-    const int32_t ex = block_excl_scan(v, sh, &tot);
-    if (b < nblk) d.blk_count[b] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) d.act_off[d.K] = carry;
+  __shared__ int32_t chunk[kScanThreads * kScanPerThread];
+  const int32_t total = scan_counts(d.blk_count, nblk, sh, chunk);
+  if (threadIdx.x == 0) d.act_off[d.K] = total;
   __syncthreads();
   for (int32_t k = threadIdx.x; k < d.K; k += blockDim.x) d.act_off[k] = d.blk_count[d.toff[k]];
   __syncthreads();
@@ -1002,8 +1045,9 @@ cudaError_t launch_scan_plan_scatter(const Dev& d, const PlanArgs& p, int T, cud
   cudaError_t e = launch_chain(k_scan_plan, dim3(1), dim3(1024), 0, st, d,
                                static_cast<int32_t>(d.n_tiles), p);
   if (e != cudaSuccess) return e;
-  return launch_chain(k_scatter_tiles, dim3(static_cast<unsigned>(d.n_tiles)), dim3(kMixJT), 0,
-                      st, d, T);
+  return launch_chain(k_scatter_tiles,
+                      dim3(blocks_for(d.n_tiles * kMixJT, kScatterThreads)),
+                      dim3(kScatterThreads), 0, st, d, T);
 }
 cudaError_t launch_plan(const Dev& d, const PlanArgs& p, cudaStream_t st) {
   return launch_chain(k_plan, dim3(1), dim3(512), 0, st, d, p);

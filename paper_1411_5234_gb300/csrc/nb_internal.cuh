@@ -75,6 +75,8 @@ struct Dev {
   double* partials = nullptr;    // part_items * 7 * NI_max
   int64_t part_items = 0;
   int32_t* blk_count = nullptr;  // n_tiles + 1 (due particles per source tile)
+  uint32_t* due_mask = nullptr;  // kMixJT / 32 words per source tile: the slots due in the
+                                 // block step (bit = lane of the slot's warp), by the predictor
   int64_t *off = nullptr, *soff = nullptr;   // K + 1
   int64_t *t_cur = nullptr, *t_min = nullptr; // K
   int32_t *act_off = nullptr, *item_off = nullptr; // K + 1
