@@ -1074,15 +1074,18 @@ cudaError_t integrator_setup() {
                               static_cast<int>(kWideSmem));
 }
 cudaError_t launch_correct(const Dev& d, const CorrectArgs& c, int64_t m_bound, cudaStream_t st) {
-  // 4 lanes per particle in 32-thread CTAs: a few hundred active particles
-  // still spread over many SMs (FP64 arithmetic, ~2 lanes per SM per clock)
-  return launch_chain(k_correct, dim3(blocks_for(4 * m_bound, 32)), dim3(32), 0, st, d, c);
+  // 4 lanes per particle; the grid strides over the active list, whose
+  // length is on the device in a block step (m_bound = N then): 128-thread
+  // CTAs, at most 4 per SM, the same lanes as 32-thread CTAs at 16 per SM but
+  // a quarter of the CTA launches when few particles are active
+  return launch_chain(k_correct, dim3(blocks_for(4 * m_bound, 128, 152 * 4)), dim3(128), 0, st,
+                      d, c);
 }
 cudaError_t launch_correct6(const Dev& d, const CorrectArgs& c, int64_t m_bound,
                             cudaStream_t st) {
-  // one thread per particle in 32-thread CTAs: few active particles still
-  // spread over many SMs (FP64 arithmetic)
-  return launch_chain(k_correct6, dim3(blocks_for(m_bound, 32)), dim3(32), 0, st, d, c);
+  // one thread per particle, grid-stride, 128-thread CTAs (as k_correct)
+  return launch_chain(k_correct6, dim3(blocks_for(m_bound, 128, 152 * 4)), dim3(128), 0, st, d,
+                      c);
 }
 cudaError_t launch_init_levels(const Dev& d, double eta_s, int T, int lmin, int lmax,
                                cudaStream_t st) {
