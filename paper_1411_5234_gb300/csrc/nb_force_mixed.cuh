@@ -247,7 +247,7 @@ constexpr int kAccTileF4 = JT / 4 * kAccGroupF4;
 template <class Sh, int NG = 0>
 __device__ __forceinline__ void tile_far(const float4* __restrict__ tile,
                                          const float4* __restrict__ acc, int ngroups,
-                                         TargetOf<Sh> (&tg)[Sh::IPT], f2 eps2) {
+                                         TargetOf<Sh> (&tg)[Sh::IPT], f2 eps2, uint32_t live) {
   const int n = NG > 0 ? NG : ngroups;
 #pragma unroll Sh::UNR
   for (int g = 0; g < n; ++g) {
@@ -259,6 +259,9 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ tile,
       const ulonglong2 ax = A[0], ay = A[1], az = A[2];
 #pragma unroll
       for (int r = 0; r < Sh::IPT; ++r) {
+        if constexpr (Sh::IPT <= 2) {
+          if (!((live >> r) & 1u)) continue;  // no active target in this row of the warp
+        }
         TargetS& s = tg[r];
         pair_tail_snap<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey),
                                   f2_add(dzh.x, s.ez), f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy),
@@ -273,6 +276,9 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ tile,
       (void)acc;
 #pragma unroll
       for (int r = 0; r < Sh::IPT; ++r) {
+        if constexpr (Sh::IPT <= 2) {
+          if (!((live >> r) & 1u)) continue;  // no active target in this row of the warp
+        }
         Target& s = tg[r];
         pair_tail<Sh, false>(s, f2_add(dxh.x, s.ex), f2_add(dyh.x, s.ey), f2_add(dzh.x, s.ez),
                              f2_add(vx.x, s.nvx), f2_add(vy.x, s.nvy), f2_add(vz.x, s.nvz), m.x,
@@ -566,6 +572,16 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
       }
       tot[r].zero(tot_sh + r * 2 * TC * NT + tid);
     }
+    // the rows of this warp's targets that hold an active target: the
+    // 2-target shapes, which serve small active sets, skip the others (with
+    // m below an item's width whole rows are empty); bit r for row r
+    uint32_t live = (1u << IPT) - 1u;
+    if constexpr (IPT <= 2) {
+      live = 0u;
+#pragma unroll
+      for (int r = 0; r < IPT; ++r)
+        if (__any_sync(0xffffffffu, valid[r])) live |= 1u << r;
+    }
 
     // pipeline stages of SJ slots (the chunk starts on a tile boundary)
     const int64_t ntile = ceil_div64(j1 - j0, SJ);  // 0: an empty piece
@@ -636,13 +652,16 @@ __global__ void __launch_bounds__(Sh::NT, Sh::MINB) k_force_mixed(const ForceArg
         }
         if (take_far) {
           if (ngq == kCellGroups)
-            tile_far<Sh, kCellGroups>(cell, cacc, ngq, tg, eps2);
+            tile_far<Sh, kCellGroups>(cell, cacc, ngq, tg, eps2, live);
           else
-            tile_far<Sh>(cell, cacc, ngq, tg, eps2);
+            tile_far<Sh>(cell, cacc, ngq, tg, eps2, live);
         } else {
           ++n_near;
 #pragma unroll
           for (int r = 0; r < IPT; ++r) {
+            if constexpr (IPT <= 2) {
+              if (!((live >> r) & 1u)) continue;
+            }
             const TargetPos tp = load_tpos(tpos, r, tid);
             float h, lx, ly, lz;
             ds_sub0(ch.x, tp.xh, tp.xl, h, lx);
