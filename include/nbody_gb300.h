@@ -1,7 +1,7 @@
 /*
  * nbody_gb300.h -- C ABI of libnbody_gb300.so: direct-summation N-body forces
- * with a 4th-order Hermite block-time-step integrator on one NVIDIA GB300
- * (sm_103a).
+ * with a 4th- or 6th-order Hermite block-time-step integrator on one NVIDIA
+ * GB300 (sm_103a).
  *
  * The library computes, for a set of "active" particles, the softened
  * Newtonian acceleration, its time derivative (jerk) and the potential due to
@@ -9,6 +9,11 @@
  * drives it with the Hermite predictor-corrector (Sec. 2 item 1) on
  * power-of-two block time steps (Sec. 2 item 2).  Several independent
  * clusters may share one context (a batch); forces never cross clusters.
+ * The i-split of Sec. 2 item 3 and the kernel shape follow a table per
+ * ceil(log2 m) that nb_autotune measures; the force sum can be split over
+ * processes (one GPU each) by pieces of the source order (nb_force_range,
+ * nb_block_force / nb_block_correct), as the paper's multi-GPU runs split it
+ * (Sec. 2.1).
  *
  * Conventions
  *   - Units: G is a parameter (default 1).  Softening eps >= 0; with eps == 0
