@@ -221,9 +221,13 @@ int nb_force_range(nb_ctx *ctx, const int32_t *active_idx, int64_t m, int32_t pa
  * into them in place (an all-reduce over the first 4 m doubles of each), on
  * the context's stream or after it.  nb_block_correct then applies the
  * corrector of Sec. 2 item 1 (nb_correct, or nb_correct_snap in order 6) to
- * those rows and closes the step.  NB_ESTATE: nb_block_force while a step is
- * open, nb_block_correct with none open, or nb_step_block while one is open.
- * Output pointers other than m_out may be NULL. */
+ * those rows and closes the step.  While a step is open, every call that
+ * does device work other than nb_block_correct (nb_predict, nb_force and its
+ * variants, nb_correct, the step calls, energies, state and derivative
+ * copies, nb_autotune, nb_resort_sources, the probes) returns NB_ESTATE:
+ * the open step's active list and force rows must stay as they are.
+ * nb_block_correct with no step open is NB_ESTATE as well.  Output pointers
+ * other than m_out may be NULL. */
 int nb_block_force(nb_ctx *ctx, int32_t part, int32_t n_parts, int64_t *m_out,
                    double **acc_rows, double **jerk_rows, double **snap_rows);
 int nb_block_correct(nb_ctx *ctx);

@@ -956,6 +956,7 @@ void nb_free(nb_ctx* c) {
 
 int nb_predict(nb_ctx* c, int64_t t_ticks) {
   NvtxRange nvtx_range("nb_predict");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || t_ticks < 0) return NB_EINVAL;
   const bool f64 = !is_mixed(c);
   NB_TRY(launch_predict(c->d, nullptr, t_ticks, c->cfg.tick_exp, !f64, f64, false, c->st));
@@ -965,6 +966,7 @@ int nb_predict(nb_ctx* c, int64_t t_ticks) {
 int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, double* jerk,
              double* pot) {
   NvtxRange nvtx_range("nb_force");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || m < 0 || m > c->d.N) return NB_EINVAL;
   if (m == 0) return NB_OK;
   if (!active_idx || !acc) return NB_EINVAL;
@@ -979,6 +981,7 @@ int nb_force(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, doubl
 int nb_force_snap(nb_ctx* c, const int32_t* active_idx, int64_t m, double* acc, double* jerk,
                   double* snap, double* pot) {
   NvtxRange nvtx_range("nb_force_snap");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || m < 0 || m > c->d.N) return NB_EINVAL;
   if (c->cfg.order != 6) return NB_ESTATE;
   if (m == 0) return NB_OK;
@@ -1083,6 +1086,7 @@ int nb_resort_sources(nb_ctx* c) {
 int nb_correct_snap(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
                     const double* acc, const double* jerk, const double* snap) {
   NvtxRange nvtx_range("nb_correct_snap");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || m < 0 || m > c->d.N || t_ticks < 0) return NB_EINVAL;
   if (c->cfg.order != 6) return NB_ESTATE;
   if (m == 0) return NB_OK;
@@ -1110,6 +1114,7 @@ int nb_correct_snap(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64
 
 int nb_get_derivs(nb_ctx* c, double* snap, double* crackle) {
   NvtxRange nvtx_range("nb_get_derivs");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c) return NB_EINVAL;
   if (c->cfg.order != 6) return NB_ESTATE;
   const int64_t N = c->d.N;
@@ -1128,6 +1133,7 @@ int nb_get_derivs(nb_ctx* c, double* snap, double* crackle) {
 
 int nb_set_derivs(nb_ctx* c, const double* snap, const double* crackle) {
   NvtxRange nvtx_range("nb_set_derivs");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || !snap || !crackle) return NB_EINVAL;
   if (c->cfg.order != 6) return NB_ESTATE;
   const int64_t N = c->d.N;
@@ -1145,6 +1151,7 @@ int nb_set_derivs(nb_ctx* c, const double* snap, const double* crackle) {
 int nb_correct(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
                const double* acc, const double* jerk) {
   NvtxRange nvtx_range("nb_correct");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || m < 0 || m > c->d.N || t_ticks < 0) return NB_EINVAL;
   if (c->cfg.order == 6) return NB_ESTATE;
   if (m == 0) return NB_OK;
@@ -1170,6 +1177,7 @@ int nb_correct(nb_ctx* c, int64_t t_ticks, const int32_t* active_idx, int64_t m,
 
 int nb_step_leapfrog(nb_ctx* c, int64_t n_steps, int64_t dt_ticks) {
   NvtxRange nvtx_range("nb_step_leapfrog");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || n_steps < 0 || dt_ticks <= 0 || dt_ticks > ((int64_t)1 << 52)) return NB_EINVAL;
   if (n_steps == 0) return NB_OK;
   const bool f64 = !is_mixed(c);
@@ -1243,6 +1251,7 @@ int nb_step_block(nb_ctx* c, int64_t n_steps, int64_t* t_ticks_out, int64_t* m_l
 }
 
 int nb_set_end_time(nb_ctx* c, int64_t t_end_ticks) {
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || t_end_ticks < 0) return NB_EINVAL;
   NB_TRY(launch_fill_i64(c->d.t_end, 1, t_end_ticks, c->st));
   return NB_OK;
@@ -1250,6 +1259,7 @@ int nb_set_end_time(nb_ctx* c, int64_t t_end_ticks) {
 
 int nb_energy(nb_ctx* c, int32_t cluster, double* ekin, double* epot) {
   NvtxRange nvtx_range("nb_energy");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || !ekin || !epot || cluster < -1 || cluster >= c->d.K) return NB_EINVAL;
   Dev& d = c->d;
   double* an = reinterpret_cast<double*>(d.acc_new);
@@ -1272,6 +1282,7 @@ int nb_energy(nb_ctx* c, int32_t cluster, double* ekin, double* epot) {
 
 int nb_energies(nb_ctx* c, double* ekin, double* epot) {
   NvtxRange nvtx_range("nb_energies");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || !ekin || !epot) return NB_EINVAL;
   Dev& d = c->d;
   double* an = reinterpret_cast<double*>(d.acc_new);
@@ -1299,6 +1310,7 @@ int nb_energies(nb_ctx* c, double* ekin, double* epot) {
 int nb_get_state(nb_ctx* c, double* pos, double* vel, double* acc, double* jerk, int64_t* t,
                  int32_t* level) {
   NvtxRange nvtx_range("nb_get_state");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c) return NB_EINVAL;
   const int64_t N = c->d.N;
   // pack (n, 3) rows into the step scratch (acc_new / jerk_new), then copy
@@ -1325,6 +1337,7 @@ int nb_get_state(nb_ctx* c, double* pos, double* vel, double* acc, double* jerk,
 int nb_set_state(nb_ctx* c, const double* pos, const double* vel, const double* acc,
                  const double* jerk, const int64_t* t, const int32_t* level) {
   NvtxRange nvtx_range("nb_set_state");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || !pos || !vel || !acc || !jerk || !t || !level) return NB_EINVAL;
   const int64_t N = c->d.N;
   const int T = c->cfg.tick_exp;
@@ -1573,6 +1586,7 @@ int nb_status(nb_ctx* c) {
 
 int nb_measure_rate(nb_ctx* c, int32_t kind, double* lanes_per_sm_clock) {
   NvtxRange nvtx_range("nb_measure_rate");
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || kind < 0 || kind > 2 || !lanes_per_sm_clock) return NB_EINVAL;
   const int per_sm = 4;
   const int ctas = c->sms * per_sm;
@@ -1616,6 +1630,7 @@ int nb_measure_rate(nb_ctx* c, int32_t kind, double* lanes_per_sm_clock) {
 }
 
 int nb_check_wait_timeout(nb_ctx* c, double seconds) {
+  if (c && c->block_open) return NB_ESTATE;  // a split block step is open
   if (!c || !(seconds > 0.0) || seconds > 10.0) return NB_EINVAL;
   int dev = 0, khz = 0;
   NB_TRY(cudaGetDevice(&dev));

@@ -132,10 +132,13 @@ def test_empty_pieces_and_bad_parts(nb):
     with pytest.raises(nb.NBError):
         sim.block_correct()                                   # no step open
     sim.block_force(0, 1)
-    with pytest.raises(nb.NBError):
-        sim.step(1)                                           # a step is open
-    with pytest.raises(nb.NBError):
-        sim.block_force(0, 1)
+    # while a split step is open, nothing may touch its active list or rows
+    for call in (lambda: sim.step(1), lambda: sim.block_force(0, 1), lambda: sim.predict(0),
+                 lambda: sim.force(act), lambda: sim.get_state(), lambda: sim.energy(),
+                 lambda: sim.resort_sources()):
+        with pytest.raises(nb.NBError) as err:
+            call()
+        assert err.value.code == nb.NB_ESTATE
     sim.block_correct()
     sim.step(1)
     assert sim.status() == nb.NB_OK
