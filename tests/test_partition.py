@@ -177,3 +177,48 @@ def test_partitioned_step_sums_before_every_correction():
     assert np.array_equal(s0, s1)
     assert np.all(s0[:4] == 3.0 * 5 * 4) and s0[4, 0] == 5
     assert "out of lockstep" in e0 and "out of lockstep" in e1
+
+
+class _FakeForceSim:
+    """A context stand-in for Partition.force: this rank's partial rows are
+    rank + 1 everywhere (the potential only when asked for)."""
+
+    def __init__(self, rank):
+        self.rank, self.stream = rank, None
+
+    def force_range(self, active, part, n_parts, want_pot=True):
+        import torch
+        assert part == self.rank and n_parts == 2
+        m = len(active)
+        acc = torch.full((m, 3), float(part + 1), dtype=torch.float64)
+        jerk = torch.full((m, 3), 10.0 * (part + 1), dtype=torch.float64)
+        pot = torch.full((m,), -float(part + 1), dtype=torch.float64) if want_pot else None
+        return acc, jerk, pot
+
+
+def _force_main(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1411_5234_gb300 import partition
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p = partition.Partition(_FakeForceSim(rank))
+    acc, jerk, pot = p.force(list(range(7)))
+    acc2, jerk2, pot2 = p.force(list(range(3)), want_pot=False)
+    np.savez(os.path.join(out_dir, f"f{rank}.npz"), acc=acc.numpy(), jerk=jerk.numpy(),
+             pot=pot.numpy(), acc2=acc2.numpy(), none=pot2 is None)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_partition_force_sums_every_row_array():
+    pytest.importorskip("torch")
+    import tempfile
+    import torch.multiprocessing as mp
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_force_main, args=(2, _free_port(), d), nprocs=2, join=True,
+                           start_method="spawn")
+        r = [dict(np.load(os.path.join(d, f"f{k}.npz"))) for k in (0, 1)]
+    for x in r:
+        assert np.all(x["acc"] == 3.0) and np.all(x["jerk"] == 30.0) and np.all(x["pot"] == -3.0)
+        assert x["acc"].shape == (7, 3) and np.all(x["acc2"] == 3.0) and bool(x["none"])
